@@ -1,0 +1,153 @@
+"""Seeded synthetic workloads for the 3D MRT lattice Boltzmann multiphase model.
+
+This module builds what both the CUDA path and the FP64 oracle take as input: the
+grid, the physical parameters of each test problem of the paper (Sec. III), and the
+initial fields.  It holds none of the method's arithmetic -- no equilibria, moments,
+stencils or collisions.  The only formulas here are the problem statements:
+
+* the static droplet phi = tanh(2(R - r)/D) (interface profile of Eq. 43 around a sphere);
+* the Rayleigh-Taylor interface h(x, y) of Eq. 42 and phi0 of Eq. 43;
+* the dimensionless groups that fix nu and the mobility: Re (Eq. 44) and the Peclet
+  number Pe = sqrt(gW) W / Mob for the Rayleigh-Taylor runs, Pe = U L / Mob (Eq. 39)
+  for interface-tracking runs.
+
+Node coordinates: along a periodic axis node i sits at i; along a walled z axis node k
+sits at k + 1/2, with the walls at z = 0 and z = nz.
+
+Arrays are float64, indexed [z, y, x] (x fastest), vectors as [3, z, y, x].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Optional, Tuple
+
+import numpy as np
+
+# Relaxation matrix of the order-parameter lattice used in the coupled runs (Eq. 45).
+SF_COUPLED = (1.0, 1.25, 1.25, 1.25, 1.2, 1.0, 1.0)
+# Relaxation matrix of the interface-tracking runs (Eq. 38).
+SF_TRACKING = (1.0, 4.0 / 3.0, 4.0 / 3.0, 4.0 / 3.0, 1.2, 1.2, 1.2)
+# Flow-lattice rates: all unity; the five viscous rates are set from nu(phi) by the solver.
+SG_UNITY = (1.0,) * 15
+
+
+@dataclass
+class Workload:
+    """One problem: grid, parameters and initial condition."""
+
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    walls_z: bool
+    rho_l: float
+    rho_g: float
+    nu_l: float
+    nu_g: float
+    mobility: float
+    D: float
+    sigma: float
+    g: Tuple[float, float, float]
+    A: float = 0.25
+    sf: Tuple[float, ...] = SF_COUPLED
+    sg: Tuple[float, ...] = SG_UNITY
+    buoyancy: bool = False
+    steps: int = 100
+    U: float = 1.0  # velocity scale used to normalise velocity errors
+    phi0: Optional[np.ndarray] = field(default=None, repr=False)
+    u0: Optional[np.ndarray] = field(default=None, repr=False)
+    p0: Optional[np.ndarray] = field(default=None, repr=False)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def node_coords(nx: int, ny: int, nz: int, walls_z: bool):
+    """Broadcastable (z, y, x) node coordinates following the convention above."""
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    y = np.arange(ny, dtype=np.float64)[None, :, None]
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+    if walls_z:
+        z = z + 0.5
+    return x, y, z
+
+
+def droplet(n: int = 32, R: float = 8.0, D: float = 4.0, sigma: float = 0.01,
+            rho_l: float = 3.0, rho_g: float = 1.0, nu: float = 0.1,
+            mobility: float = 0.1, steps: int = 500, nx: Optional[int] = None,
+            ny: Optional[int] = None, nz: Optional[int] = None) -> Workload:
+    """Static droplet of radius R centred in a periodic box; phi = +1 (rho_l) inside."""
+    nx = n if nx is None else nx
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    x, y, z = node_coords(nx, ny, nz, False)
+    r = np.sqrt((x - nx / 2) ** 2 + (y - ny / 2) ** 2 + (z - nz / 2) ** 2)
+    phi0 = np.tanh(2.0 * (R - r) / D)
+    return Workload(name=f"droplet{nx}x{ny}x{nz}_R{R:g}", nx=nx, ny=ny, nz=nz,
+                    walls_z=False, rho_l=rho_l, rho_g=rho_g, nu_l=nu, nu_g=nu,
+                    mobility=mobility, D=D, sigma=sigma, g=(0.0, 0.0, 0.0),
+                    sf=SF_COUPLED, steps=steps, U=sigma / (rho_l * nu), phi0=phi0)
+
+
+def rayleigh_taylor(W: int = 64, Re: float = 256.0, atwood: float = 0.5,
+                    sqrt_gW: float = 0.04, D: float = 4.0, sigma: float = 1e-4,
+                    Pe: float = 50.0, rho_g: float = 1.0, steps: int = 20000,
+                    nz: Optional[int] = None) -> Workload:
+    """Rayleigh-Taylor box W x W x 4W: heavy fluid (phi = +1) above z = 2W + h(x, y).
+
+    Eq. 42 gives h, Eq. 43 phi0 and Eq. 44 Re = sqrt(gW) W / nu; the mobility follows
+    from Pe = sqrt(gW) W / Mob.  Lateral boundaries periodic, z walled.
+    """
+    nz = 4 * W if nz is None else nz
+    rho_l = rho_g * (1.0 + atwood) / (1.0 - atwood)
+    gacc = sqrt_gW ** 2 / W
+    nu = sqrt_gW * W / Re
+    mob = sqrt_gW * W / Pe
+    x, y, z = node_coords(W, W, nz, True)
+    h = 0.05 * W * (np.cos(2 * math.pi * x / W) + np.cos(2 * math.pi * y / W))
+    phi0 = np.tanh(2.0 * (z - h - nz / 2.0) / D)
+    phi0 = np.broadcast_to(phi0, (nz, W, W)).copy()
+    return Workload(name=f"rt{W}x{W}x{nz}_Re{Re:g}", nx=W, ny=W, nz=nz, walls_z=True,
+                    rho_l=rho_l, rho_g=rho_g, nu_l=nu, nu_g=nu, mobility=mob, D=D,
+                    sigma=sigma, g=(0.0, 0.0, -gacc), sf=SF_COUPLED, steps=steps,
+                    U=sqrt_gW, phi0=phi0)
+
+
+def flat_interface(nz: int = 32, nxy: int = 4, D: float = 4.0, sigma: float = 0.01,
+                   rho_l: float = 3.0, rho_g: float = 1.0, nu: float = 0.1,
+                   mobility: float = 0.1, steps: int = 2000) -> Workload:
+    """Planar interface phi = tanh(2(z - nz/2)/D) between two z walls, no gravity."""
+    x, y, z = node_coords(nxy, nxy, nz, True)
+    phi0 = np.broadcast_to(np.tanh(2.0 * (z - nz / 2.0) / D), (nz, nxy, nxy)).copy()
+    return Workload(name=f"flat{nxy}x{nxy}x{nz}", nx=nxy, ny=nxy, nz=nz, walls_z=True,
+                    rho_l=rho_l, rho_g=rho_g, nu_l=nu, nu_g=nu, mobility=mobility, D=D,
+                    sigma=sigma, g=(0.0, 0.0, 0.0), sf=SF_COUPLED, steps=steps,
+                    U=sigma / (rho_l * nu), phi0=phi0)
+
+
+def perturbed(w: Workload, seed: int = 0, phi_amp: float = 0.0, u_amp: float = 0.0,
+              p_amp: float = 0.0) -> Workload:
+    """Copy of `w` with seeded random perturbations of phi0, u0 and p0.
+
+    Parity runs use this so that every term of the update (velocity-dependent
+    equilibria and sources, pressure) is exercised from the first step.  The phi
+    perturbation is kept inside [-1, 1].
+    """
+    rng = np.random.default_rng(seed)
+    phi0 = w.phi0.copy()
+    if phi_amp:
+        phi0 = np.clip(phi0 + phi_amp * rng.uniform(-1, 1, phi0.shape), -1.0, 1.0)
+    u0 = None if not u_amp else u_amp * rng.uniform(-1, 1, (3,) + w.shape)
+    p0 = None if not p_amp else p_amp * rng.uniform(-1, 1, w.shape)
+    return replace(w, name=w.name + f"_pert{seed}", phi0=phi0, u0=u0, p0=p0)
+
+
+def random_fields(shape, seed: int = 0, scale: float = 1.0) -> np.ndarray:
+    """Uniform(-scale, scale) float64 array, seeded."""
+    return scale * np.random.default_rng(seed).uniform(-1.0, 1.0, shape)
