@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled D3Q15 + D3Q7 MRT multiphase update on GB300.
+
+One benchmark step is one full time step of the solver over the whole grid (order
+parameter pass, chemical-potential pass, fused stream-collide pass).  The workload is
+the Rayleigh-Taylor instability at Re = 4000, At = 0.5 on a 256 x 256 x 1024 grid
+(67M cells, FP32 storage), initial condition of Eqs. 42-43.
+
+Printed JSON line (rank 0):
+  value      MLUPS (million cell updates per second) over all ranks, device-timed with
+             CUDA events around exactly --steps steps; inputs resident in HBM.
+  e2e        the same metric through the public C ABI with host buffers: pinned-host
+             phi0 uploaded by lbm_init_phi, every step followed by lbm_reduce (FP64 mass
+             and momentum, read back to the host), lbm_read_fields (phi, u, p) at the end.
+  roofline   the fused stream-collide kernel: algorithmic bytes per launch / its mean
+             CUDA-event duration, against the measured HBM copy bandwidth.
+  cpu_baseline  the FP64 oracle, single-threaded, on a bounded sample (rank 0, N = 1).
+With --impl reference the oracle alone is timed on the host cores (the reference arm).
+Under torchrun each rank runs an independent replica (weak scaling, no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled D3Q15+D3Q7 MLUPS"
+UNIT = "MLUPS"
+
+# Algorithmic bytes per cell of the fused stream-collide kernel, FP32: read f (7) and
+# g (15) populations, phi u of the previous step (3), phi and mu at the cell (2); write
+# f, g and phi u (25).  The neighbour values of phi and mu are re-reads of the same two
+# planes, which the kernel is meant to serve from cache.
+COLLIDE_BYTES_PER_CELL = (22 + 3 + 2) * 4 + (22 + 3) * 4
+STEP_BYTES_PER_CELL = COLLIDE_BYTES_PER_CELL + (7 + 1) * 4 + (1 + 1) * 4  # + k_phi + k_mu
+
+# DRAM traffic of k_collide per cell from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the cells of the captured launch), valid only for
+# the kernel source it was taken on (hash of csrc/lbm_device.cuh + lbm_kernels.cu).
+NCU_TRAFFIC = {}
+
+WORKLOADS = {
+    "rt256": dict(W=256, Re=4000.0, desc="Rayleigh-Taylor 256x256x1024, Re=4000, At=0.5, "
+                                        "sqrt(gW)=0.04, D=4, sigma=1e-4, Pe=50, FP32 storage"),
+    "rt128": dict(W=128, Re=1024.0, desc="Rayleigh-Taylor 128x128x512, Re=1024, At=0.5"),
+    "rt64": dict(W=64, Re=256.0, desc="Rayleigh-Taylor 64x64x256, Re=256, At=0.5"),
+}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("lbm_device.cuh", "lbm_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1507_07294_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks ------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.lines = []
+        self._thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self._thread = threading.Thread(target=self._read, daemon=True)
+        self._thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._thread:
+            self._thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- CPU oracle ------
+ORACLE_CHILD = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+from oracle import lbm_oracle as O
+from paper_1507_07294_gb300 import inputs as I
+W, Re, nz, warm, steps_max, budget = {W}, {Re}, {nz}, {warm}, {steps_max}, {budget}
+w = I.rayleigh_taylor(W=W, Re=Re, nz=nz)
+o = O.Oracle(O.Params.from_workload(w))
+o.init(w.phi0)
+o.step(max(1, warm))
+t0 = time.perf_counter(); n = 0
+while n < steps_max and (n < 1 or time.perf_counter() - t0 < budget):
+    o.step(1); n += 1
+dt = time.perf_counter() - t0
+print(json.dumps({{"cells": w.cells, "steps": n, "seconds": dt, "grid": [w.nx, w.ny, w.nz]}}))
+"""
+
+
+def run_oracle_sample(W: int, Re: float, nz: int, steps_max: int, budget_s: float,
+                      warm: int = 1) -> dict:
+    """Time the FP64 oracle in a fresh single-threaded interpreter (spawned, so no CUDA
+    state is inherited)."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = "1"
+    code = ORACLE_CHILD.format(root=ROOT, W=W, Re=Re, nz=nz, warm=warm, steps_max=steps_max,
+                               budget=budget_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["mlups"] = d["cells"] * d["steps"] / d["seconds"] / 1e6
+    return d
+
+
+def oracle_baseline(budget_s: float = 15.0) -> dict:
+    d = run_oracle_sample(64, 4000.0, 256, 50, budget_s)
+    return {"value": round(d["mlups"], 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, single thread, Rayleigh-Taylor setup at Re=4000 on the "
+                      f"64x64x256 crop, {d['steps']} steps after 1 untimed step, "
+                      f"{d['seconds']:.1f} s"}
+
+
+# ------------------------------------------------------------------ helpers ------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def config_dict(args, w, world):
+    spec = WORKLOADS[args.workload]
+    return {"workload": f"{args.workload}: {spec['desc']}",
+            "grid": [w.nx, w.ny, w.nz], "cells": w.cells, "walls_z": bool(w.walls_z),
+            "storage": "fp32", "aa_in_place_streaming": True,
+            "l2": f"state {w.cells * 100 / 1e9:.1f} GB (f, g, phi u) > 129 MB L2: no flush needed",
+            "parallelism": f"replicas x{world} (independent runs per GPU)"}
+
+
+# ------------------------------------------------------------ reference arm -----
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1507_07294_gb300 import inputs as I
+    spec = WORKLOADS[args.workload]
+    w = I.rayleigh_taylor(W=spec["W"], Re=spec["Re"])
+    # Each reference step is one oracle step on a bounded sample of the workload: the
+    # 64-wide crop of the same setup, depth shrunk so W + K steps fit ~150 s.
+    total = args.warmup + args.steps
+    probe = run_oracle_sample(64, spec["Re"], 64, 1, 0.0)  # calibration
+    per_cell = probe["seconds"] / probe["cells"]
+    nz = int(max(16, min(256, 150.0 / max(total, 1) / per_cell / (64 * 64))))
+    d = run_oracle_sample(64, spec["Re"], nz, args.steps, 1e9, warm=args.warmup)
+    value = d["mlups"]
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * d["seconds"] / d["steps"], 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: Rayleigh-Taylor initial condition (Eqs. 42-43)",
+            "config": config_dict(args, w, world),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 numpy oracle, single thread, one step per bench step "
+                                       f"on a 64x64x{nz} slab of the same setup"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm ------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = torch.cuda.current_device()
+
+    from paper_1507_07294_gb300 import inputs as I
+    from paper_1507_07294_gb300 import lbm as L
+
+    spec = WORKLOADS[args.workload]
+    w = I.rayleigh_taylor(W=spec["W"], Re=spec["Re"])
+    stream = torch.cuda.current_stream()
+    solver = L.Solver(w, stream=stream.cuda_stream)
+    ctx = solver.ctx
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-timed region -------------------------------------------------
+    solver.step(args.warmup)
+    L.lbm_profile(ctx, True)
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    barrier()
+    clock = clocks.stop()
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1))
+    kernels = {}
+    for k, name in enumerate(L.KERNEL_NAMES):
+        ms, n = L.lbm_profile_read(ctx, k)
+        kernels[name] = {"launches": n, "total_ms": round(ms, 4),
+                         "mean_ms": round(ms / max(n, 1), 5)}
+    L.lbm_profile(ctx, False)
+    sum_phi, _ = solver.reduce()  # the run stayed finite
+
+    cells = w.cells
+    value = cells * args.steps * world / (elapsed_ms * 1e-3) / 1e6
+    coll_ms = kernels["k_collide"]["mean_ms"]
+    peak, peak_kind = measured_peaks()
+    achieved = COLLIDE_BYTES_PER_CELL * cells / (coll_ms * 1e-3) / 1e9
+    src_hash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get("k_collide")
+    traffic = round(tr["bytes_per_cell"] * cells) if tr and tr.get("kernel_sha") == src_hash else None
+
+    # ---- end-to-end region through the C ABI with host buffers ---------------
+    e2e = None
+    if not args.no_e2e:
+        phi_host = torch.empty(cells, dtype=torch.float64, pin_memory=True).numpy()
+        phi_host[:] = w.phi0.reshape(-1)
+        barrier()
+        t0 = time.perf_counter()
+        L.lbm_init_phi(ctx, phi_host)
+        for _ in range(args.steps):
+            L.lbm_step(ctx, 1)
+            L.lbm_reduce(ctx)
+        out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P)
+        barrier()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        assert np.isfinite(out["phi"]).all()
+        e2e = {"value": round(cells * args.steps * world / t_e2e / 1e6, 3), "unit": UNIT,
+               "h2d_bytes_per_step": round(8 * cells / args.steps),
+               "d2h_bytes_per_step": round(5 * 8 + 5 * 4 * cells / args.steps),
+               "seconds": round(t_e2e, 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic: Rayleigh-Taylor initial condition (Eqs. 42-43), no dataset",
+                "config": config_dict(args, w, world),
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                             "kernel": "k_collide",
+                             "bytes_per_cell": COLLIDE_BYTES_PER_CELL,
+                             "peak_source": f"{peak_kind} HBM copy bandwidth"},
+                "step_bytes_per_cell": STEP_BYTES_PER_CELL,
+                "step_hbm_frac": round(STEP_BYTES_PER_CELL * cells * args.steps /
+                                       (elapsed_ms * 1e-3) / 1e9 / peak, 4),
+                "kernels": kernels,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
+                "gpu_launches": 3 * args.steps,
+                "sum_phi": sum_phi}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rt256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * lbm.h -- C ABI of a GB300 (sm_103a) solver for the three-dimensional MRT lattice
+ * Boltzmann model for multiphase flow of Liang, Shi and Chai (arXiv:1507.07294).
+ *
+ * One time step couples two lattices on a regular grid of nx * ny * nz cells:
+ *   - a D3Q7 lattice f_i for the Cahn-Hilliard equation of the order parameter phi
+ *     (Sec. II A, Eqs. 4-19), and
+ *   - a D3Q15 lattice g_i for the incompressible Navier-Stokes equations with pressure
+ *     p and velocity u (Sec. II B, Eqs. 20-33),
+ * with the isotropic difference schemes of Eqs. 34-36 for grad(phi), lap(phi) and
+ * lap(mu).  Lattice units: c = dx = dt = 1.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an lbm_status; nothing throws across the ABI.  After a
+ *     failure lbm_last_error(ctx) holds a one-line message.
+ *   - Host arrays hold one value per cell, x fastest: index (z * ny + y) * nx + x.
+ *     Vector fields are planar: component a of cell c at a * N + c, N = nx * ny * nz.
+ *     The caller owns every host buffer; the library copies in or out before it
+ *     returns.
+ *   - Device state is owned by the context.  It is allocated through the caller's
+ *     lbm_allocator (or cudaMalloc when none is given) and released by lbm_destroy.
+ *   - All device work runs on the CUDA stream given to lbm_create (0 = the legacy
+ *     default stream).  lbm_step only enqueues work; calls that return data to the
+ *     host synchronise that stream.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,     /* bad argument: null pointer, size, parameter out of range  */
+  LBM_ENOMEM = 2,     /* the allocator returned NULL                               */
+  LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error)    */
+  LBM_EUNSTABLE = 4,  /* a non-finite value was found by lbm_reduce                */
+  LBM_ETIMEOUT = 5,   /* reserved: a device-side wait ran out                      */
+  LBM_EBUSY = 6       /* reserved                                                  */
+} lbm_status;
+
+/* Grid.  x and y are periodic.  walls_z = 0: z periodic too; walls_z = 1: no-slip
+ * walls at z = 0 and z = nz (node k at z = k + 1/2), closed by halfway bounce-back of
+ * both f and g.  The paper names the no-slip condition (Sec. III C) but not the scheme;
+ * the difference stencils see a ghost layer equal to the adjacent fluid node. */
+typedef struct {
+  int nx, ny, nz;
+  int walls_z;
+} lbm_grid;
+
+/* Flags for lbm_params.flags. */
+#define LBM_FLAG_BUOYANCY 1u /* G = (rho - (rho_l + rho_g)/2) g instead of G = rho g */
+
+/* Storage types for lbm_params.storage. */
+#define LBM_STORAGE_FP32 0
+
+/* Physical and lattice parameters (the problem statement of Sec. II). */
+typedef struct {
+  double rho_l, rho_g; /* phase densities; rho(phi) by Eq. 14, phi = +1 is rho_l      */
+  double nu_l, nu_g;   /* kinematic viscosities; nu(phi) = (1+phi)/2 nu_l +
+                          (1-phi)/2 nu_g, and lambda_9..13 = 1/(nu(phi)/c_s^2 + 1/2)
+                          per cell (Eq. 33, c_s^2 = 1/3)                            */
+  double mobility;     /* Mob of Eq. 1; eta = Mob / (A (1/s_1 - 1/2)) by Eq. 19      */
+  double D, sigma;     /* interface width and surface tension: kappa = 3 D sigma / 8,
+                          beta = 3 sigma / (4 D) (text after Eq. 2)                  */
+  double g[3];         /* body acceleration; the external force is G = rho g         */
+  double A;            /* free parameter of the D3Q7 weights, 0 < A < 1/3 (Eq. 8)   */
+  double sf[7];        /* S^f = diag(s_0..s_6), 0 < s_i < 2, s_1 = s_2 = s_3 (Eq. 10)*/
+  double sg[15];       /* S^g = diag(lambda_0..lambda_14), 0 < lambda < 2 (Eq. 26);
+                          lambda_9..13 are ignored: they follow nu(phi)              */
+  unsigned flags;      /* LBM_FLAG_*                                                  */
+  int storage;         /* LBM_STORAGE_FP32                                            */
+} lbm_params;
+
+/* Device allocator.  alloc returns device memory of at least `bytes` bytes (aligned
+ * to 256 bytes) or NULL; free releases it.  Calls happen inside lbm_create,
+ * lbm_init_phi and lbm_destroy only. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} lbm_allocator;
+
+/* Field selection for lbm_read_fields. */
+#define LBM_FIELD_PHI 1u
+#define LBM_FIELD_RHO 2u
+#define LBM_FIELD_P 4u
+#define LBM_FIELD_U 8u
+#define LBM_FIELD_MU 16u
+
+/* Create a solver for `grid` and `params`.  `alloc` may be NULL (cudaMalloc is then
+ * used); `cuda_stream` is a cudaStream_t or NULL.  Fails with LBM_EINVAL when a size
+ * is < 1, N >= 2^31, a rate is outside (0, 2), s_1..3 differ, A is outside (0, 1/3),
+ * a density or viscosity is not positive, or the storage type is unknown.
+ * Device memory: 22 populations + phi u (3) + phi + mu + 5 staging floats per cell,
+ * i.e. 128 bytes per cell in FP32. */
+lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
+                      const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out);
+
+/* Initial condition (Sec. III): phi (N values, host) and optionally u (3N, planar)
+ * and p (N); NULL means zero.  mu follows from phi by Eq. 2 with the stencil of
+ * Eq. 36; f and g are set to their equilibria f^eq (Eq. 5) and g^eq (Eq. 21).  Resets
+ * the step count to 0; the first step after it takes d_t(phi u) = 0 (Eq. 34 has no
+ * earlier value).  Synchronises the stream. */
+lbm_status lbm_init_phi(lbm_ctx* ctx, const double* phi, const double* u, const double* p);
+
+/* Advance n >= 0 time steps (Eqs. 4 and 20: stream, then collide in moment space with
+ * Eqs. 17-18 and 31-32).  Asynchronous on the context's stream. */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields at the current time, computed on the device from the current
+ * populations: phi (Eq. 13), rho (Eq. 14), p (Eq. 30), u (Eq. 29, planar 3N) and mu
+ * (Eq. 2).  Only the fields selected in `mask` are written; the others may be NULL.
+ * Values are computed in FP32 and widened to double.  Synchronises the stream. */
+lbm_status lbm_read_fields(lbm_ctx* ctx, unsigned mask, double* phi, double* rho,
+                           double* p, double* u, double* mu);
+
+/* Global sums in FP64 on the device: sum_x phi and sum_x sum_i c_i g_i (the lattice
+ * momentum of the current populations).  Summation order is fixed, so results are
+ * reproducible run to run.  Returns LBM_EUNSTABLE (sums still written) if any phi or
+ * momentum value is not finite.  Synchronises the stream. */
+lbm_status lbm_reduce(lbm_ctx* ctx, double* sum_phi, double mom[3]);
+
+/* Full state in the paper's velocity order (Eqs. 6 and 23): the populations at the
+ * current time just after propagation, f (7N) and g (15N), planar by population, and
+ * the phi u of the previous step (3N, planar; all zero while no step has been taken
+ * since lbm_init_phi).  FP32 exactly as stored.  Any output may be NULL.  `step`
+ * receives the step count.  Synchronises the stream. */
+lbm_status lbm_read_state(lbm_ctx* ctx, float* f, float* g, float* phiu_prev,
+                          long long* step);
+
+/* Replace the state (same layout as lbm_read_state).  When phiu_prev is NULL or step
+ * is 0, the next step takes d_t(phi u) = 0, as after lbm_init_phi.  Resuming from a
+ * state read by lbm_read_state reproduces the original run bit for bit.  Synchronises
+ * the stream. */
+lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
+                           const float* phiu_prev, long long step);
+
+/* Number of steps taken since lbm_init_phi / lbm_write_state. */
+lbm_status lbm_get_step(const lbm_ctx* ctx, long long* step);
+
+/* Per-kernel timing with CUDA events on the context's stream.  While enabled,
+ * lbm_step brackets each kernel launch with events.  lbm_profile_read synchronises,
+ * then returns for kernel k (0: order parameter, 1: chemical potential, 2: fused
+ * stream-collide) the summed duration in ms and the number of launches since the
+ * last lbm_profile(ctx, 1). */
+lbm_status lbm_profile(lbm_ctx* ctx, int enable);
+lbm_status lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms,
+                            long long* launches);
+
+/* Release all device memory of the context and the context itself. */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none); for ctx == NULL, the message of the
+ * last lbm_create failure in this process. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,418 @@
+// C ABI of the solver (declared in include/lbm.h): context life cycle, parameter
+// mapping, allocation through the caller's allocator, and the launch sequence of one
+// time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+struct lbm_ctx {
+  lbm_grid grid{};
+  lbm_params params{};
+  lbm::Geometry geo{};
+  lbm::Physics ph{};
+  lbm_allocator alloc{};
+  bool have_alloc = false;
+  cudaStream_t stream = nullptr;
+
+  // device memory
+  float* pop = nullptr;    // 22 populations, AA layout, stride geo.stride
+  float* phiu = nullptr;   // phi u of the previous step, 3 planes
+  float* phi = nullptr;    // order parameter of the current step
+  float* mu = nullptr;     // chemical potential of the current step
+  float* stage = nullptr;  // 5 planes: field read-out, state gather, init inputs
+  double* partial = nullptr;  // reduction partials
+  double* red = nullptr;      // 5 reduction results
+
+  long long step = 0;
+  bool odd = false;        // AA parity of the stored populations
+  bool have_prev = false;  // phiu holds the previous step's phi u
+  bool initialized = false;
+
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events[3];
+
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbm_status fail(lbm_ctx* ctx, lbm_status st, const std::string& msg) {
+  if (ctx)
+    ctx->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+lbm_status fail_cuda(lbm_ctx* ctx, const char* what, cudaError_t e) {
+  return fail(ctx, LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CK(ctx, call)                                        \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return fail_cuda((ctx), #call, e_);   \
+  } while (0)
+
+void* dev_alloc(lbm_ctx* c, size_t bytes) {
+  if (c->have_alloc) return c->alloc.alloc(bytes, c->alloc.user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dev_free(lbm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->have_alloc)
+    c->alloc.free(p, c->alloc.user);
+  else
+    cudaFree(p);
+}
+
+bool rate_ok(double s) { return s > 0.0 && s < 2.0 && std::isfinite(s); }
+
+// Float copies of the derived parameters (Eqs. 2, 14, 19, 33).
+lbm::Physics make_physics(const lbm_params& p) {
+  lbm::Physics ph{};
+  ph.rho_g = static_cast<float>(p.rho_g);
+  ph.half_drho = static_cast<float>(0.5 * (p.rho_l - p.rho_g));
+  ph.nu_g = static_cast<float>(p.nu_g);
+  ph.nu_mid = static_cast<float>(0.5 * (p.nu_l + p.nu_g));
+  ph.half_dnu = static_cast<float>(0.5 * (p.nu_l - p.nu_g));
+  ph.mob = static_cast<float>(p.mobility);
+  ph.kappa = static_cast<float>(3.0 * p.D * p.sigma / 8.0);
+  ph.beta = static_cast<float>(3.0 * p.sigma / (4.0 * p.D));
+  ph.A = static_cast<float>(p.A);
+  ph.eta = static_cast<float>(p.mobility / (p.A * (1.0 / p.sf[1] - 0.5)));
+  for (int a = 0; a < 3; ++a) ph.gacc[a] = static_cast<float>(p.g[a]);
+  ph.rho_ref = (p.flags & LBM_FLAG_BUOYANCY) ? static_cast<float>(0.5 * (p.rho_l + p.rho_g)) : 0.0f;
+  for (int k = 0; k < 7; ++k) ph.sf[k] = static_cast<float>(p.sf[k]);
+  for (int k = 0; k < 15; ++k) ph.sg[k] = static_cast<float>(p.sg[k]);
+  return ph;
+}
+
+lbm_status validate(const lbm_grid* g, const lbm_params* p) {
+  if (!g || !p) return fail(nullptr, LBM_EINVAL, "grid and params must not be NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+    return fail(nullptr, LBM_EINVAL, "grid sizes must be >= 1");
+  const long long n = static_cast<long long>(g->nx) * g->ny * g->nz;
+  if (n >= (1LL << 31) - 64) return fail(nullptr, LBM_EINVAL, "grid has 2^31 cells or more");
+  if (g->walls_z != 0 && g->walls_z != 1) return fail(nullptr, LBM_EINVAL, "walls_z must be 0 or 1");
+  if (!(p->rho_l > 0 && p->rho_g > 0)) return fail(nullptr, LBM_EINVAL, "densities must be > 0");
+  if (!(p->nu_l > 0 && p->nu_g > 0)) return fail(nullptr, LBM_EINVAL, "viscosities must be > 0");
+  if (!(p->mobility >= 0 && std::isfinite(p->mobility)))
+    return fail(nullptr, LBM_EINVAL, "mobility must be >= 0");
+  if (!(p->D > 0 && std::isfinite(p->sigma))) return fail(nullptr, LBM_EINVAL, "D must be > 0");
+  if (!(p->A > 0 && p->A < 1.0 / 3.0)) return fail(nullptr, LBM_EINVAL, "A must lie in (0, 1/3)");
+  for (int k = 0; k < 7; ++k)
+    if (!rate_ok(p->sf[k])) return fail(nullptr, LBM_EINVAL, "sf rates must lie in (0, 2)");
+  for (int k = 0; k < 15; ++k)
+    if ((k < 9 || k > 13) && !rate_ok(p->sg[k]))
+      return fail(nullptr, LBM_EINVAL, "sg rates must lie in (0, 2)");
+  if (!(p->sf[1] == p->sf[2] && p->sf[2] == p->sf[3]))
+    return fail(nullptr, LBM_EINVAL, "Eq. 19 needs s_1 = s_2 = s_3");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->g[a])) return fail(nullptr, LBM_EINVAL, "g must be finite");
+  if (p->storage != LBM_STORAGE_FP32) return fail(nullptr, LBM_EINVAL, "unknown storage type");
+  return LBM_OK;
+}
+
+void release(lbm_ctx* c) {
+  for (auto& list : c->events)
+    for (auto& pr : list) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  dev_free(c, c->pop);
+  dev_free(c, c->phiu);
+  dev_free(c, c->phi);
+  dev_free(c, c->mu);
+  dev_free(c, c->stage);
+  dev_free(c, c->partial);
+  dev_free(c, c->red);
+  c->pop = c->phiu = c->phi = c->mu = c->stage = nullptr;
+  c->partial = c->red = nullptr;
+}
+
+template <typename F>
+cudaError_t timed(lbm_ctx* c, int kernel, F&& launch) {
+  if (!c->profiling) return launch();
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&b);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(a, c->stream);
+  e = launch();
+  cudaEventRecord(b, c->stream);
+  c->events[kernel].emplace_back(a, b);
+  return e;
+}
+
+// Copy N floats of a device plane to host doubles.
+lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, std::vector<float>& tmp) {
+  const size_t n = static_cast<size_t>(c->geo.n);
+  tmp.resize(n);
+  LBM_CK(c, cudaMemcpyAsync(tmp.data(), dev, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < n; ++i) host[i] = tmp[i];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_allocator* alloc,
+                      void* cuda_stream, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  lbm_status st = validate(grid, params);
+  if (st != LBM_OK) return st;
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(nullptr, LBM_EINVAL, "allocator needs both alloc and free");
+
+  lbm_ctx* c = new lbm_ctx();
+  c->grid = *grid;
+  c->params = *params;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->have_alloc = true;
+  }
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  const long long n = static_cast<long long>(grid->nx) * grid->ny * grid->nz;
+  c->geo.nx = grid->nx;
+  c->geo.ny = grid->ny;
+  c->geo.nz = grid->nz;
+  c->geo.walls = grid->walls_z;
+  c->geo.n = static_cast<int>(n);
+  c->geo.plane = grid->nx * grid->ny;
+  c->geo.stride = static_cast<size_t>((n + 63) / 64 * 64);  // 256-byte aligned planes
+  c->ph = make_physics(*params);
+
+  const size_t plane = c->geo.stride * sizeof(float);
+  c->pop = static_cast<float*>(dev_alloc(c, plane * lbm::kSlots));
+  c->phiu = static_cast<float*>(dev_alloc(c, plane * 3));
+  c->phi = static_cast<float*>(dev_alloc(c, plane));
+  c->mu = static_cast<float*>(dev_alloc(c, plane));
+  c->stage = static_cast<float*>(dev_alloc(c, plane * 5));
+  c->partial = static_cast<double*>(dev_alloc(c, sizeof(double) * 5 * lbm::kReduceMaxParts));
+  c->red = static_cast<double*>(dev_alloc(c, sizeof(double) * 8));
+  if (!c->pop || !c->phiu || !c->phi || !c->mu || !c->stage || !c->partial || !c->red) {
+    release(c);
+    delete c;
+    return fail(nullptr, LBM_ENOMEM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(c->pop, 0, plane * lbm::kSlots, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->phiu, 0, plane * 3, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    release(c);
+    delete c;
+    return fail(nullptr, LBM_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const double* p) {
+  if (!c) return LBM_EINVAL;
+  if (!phi) return fail(c, LBM_EINVAL, "phi must not be NULL");
+  const size_t n = static_cast<size_t>(c->geo.n);
+  const size_t s = c->geo.stride;
+  double* tmp = static_cast<double*>(dev_alloc(c, n * sizeof(double)));
+  if (!tmp) return fail(c, LBM_ENOMEM, "device allocation failed (init staging)");
+  auto upload = [&](const double* host, float* dst) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(tmp, host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    return lbm::launch_convert(tmp, dst, c->geo.n, c->stream);
+  };
+  cudaError_t e = upload(phi, c->phi);
+  if (e == cudaSuccess && u)
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = upload(u + a * n, c->stage + a * s);
+  if (e == cudaSuccess && p) e = upload(p, c->stage + 3 * s);
+  if (e == cudaSuccess) e = lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream);
+  if (e == cudaSuccess)
+    e = lbm::launch_init(c->pop, c->phiu, c->phi, c->mu, u ? c->stage : nullptr,
+                         p ? c->stage + 3 * s : nullptr, c->geo, c->ph, c->stream);
+  const cudaError_t es = cudaStreamSynchronize(c->stream);
+  dev_free(c, tmp);
+  if (e != cudaSuccess) return fail_cuda(c, "lbm_init_phi", e);
+  if (es != cudaSuccess) return fail_cuda(c, "lbm_init_phi", es);
+  c->step = 0;
+  c->odd = false;
+  c->have_prev = false;
+  c->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int n) {
+  if (!c) return LBM_EINVAL;
+  if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  for (int it = 0; it < n; ++it) {
+    const bool odd = c->odd;
+    LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(c->pop, c->phi, c->geo, odd, c->stream); }));
+    LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
+    const bool prev = c->have_prev;
+    LBM_CK(c, timed(c, 2, [&] {
+             return lbm::launch_collide(c->pop, c->phiu, c->phi, c->mu, c->geo, c->ph, odd, prev,
+                                        c->stream);
+           }));
+    c->odd = !c->odd;
+    c->have_prev = true;
+    ++c->step;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, double* p,
+                           double* u, double* mu) {
+  if (!c) return LBM_EINVAL;
+  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (((mask & LBM_FIELD_PHI) && !phi) || ((mask & LBM_FIELD_RHO) && !rho) ||
+      ((mask & LBM_FIELD_P) && !p) || ((mask & LBM_FIELD_U) && !u) || ((mask & LBM_FIELD_MU) && !mu))
+    return fail(c, LBM_EINVAL, "a selected field has a NULL buffer");
+  LBM_CK(c, lbm::launch_phi(c->pop, c->phi, c->geo, c->odd, c->stream));
+  LBM_CK(c, lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream));
+  if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
+    LBM_CK(c, lbm::launch_fields(c->pop, c->phi, c->mu, c->stage, c->geo, c->ph, c->odd, c->stream));
+  const size_t n = static_cast<size_t>(c->geo.n);
+  const size_t s = c->geo.stride;
+  std::vector<float> tmp;
+  lbm_status st = LBM_OK;
+  if (mask & LBM_FIELD_PHI) st = plane_to_host(c, c->phi, phi, tmp);
+  if (st == LBM_OK && (mask & LBM_FIELD_MU)) st = plane_to_host(c, c->mu, mu, tmp);
+  if (st == LBM_OK && (mask & LBM_FIELD_RHO)) st = plane_to_host(c, c->stage, rho, tmp);
+  if (st == LBM_OK && (mask & LBM_FIELD_P)) st = plane_to_host(c, c->stage + s, p, tmp);
+  for (int a = 0; a < 3 && st == LBM_OK && (mask & LBM_FIELD_U); ++a)
+    st = plane_to_host(c, c->stage + (2 + a) * s, u + a * n, tmp);
+  if (st == LBM_OK) LBM_CK(c, cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
+  if (!c) return LBM_EINVAL;
+  if (!sum_phi || !mom) return fail(c, LBM_EINVAL, "outputs must not be NULL");
+  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  LBM_CK(c, lbm::launch_phi(c->pop, c->phi, c->geo, c->odd, c->stream));
+  LBM_CK(c, lbm::launch_reduce(c->pop, c->phi, c->partial, c->red, c->geo, c->odd, c->stream));
+  double h[5];
+  LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  *sum_phi = h[0];
+  mom[0] = h[1];
+  mom[1] = h[2];
+  mom[2] = h[3];
+  if (h[4] > 0) return fail(c, LBM_EUNSTABLE, "non-finite phi or momentum in " +
+                                                  std::to_string(static_cast<long long>(h[4])) + " cells");
+  return LBM_OK;
+}
+
+lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long long* step) {
+  if (!c) return LBM_EINVAL;
+  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  const size_t n = static_cast<size_t>(c->geo.n);
+  for (int q = 0; q < lbm::kSlots; ++q) {
+    float* dst = q < 7 ? (f ? f + q * n : nullptr) : (g ? g + (q - 7) * n : nullptr);
+    if (!dst) continue;
+    LBM_CK(c, lbm::launch_gather(c->pop, c->stage, c->geo, c->odd, q, c->stream));
+    LBM_CK(c, cudaMemcpyAsync(dst, c->stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (phiu_prev) {
+    if (c->have_prev) {
+      for (int a = 0; a < 3; ++a)
+        LBM_CK(c, cudaMemcpyAsync(phiu_prev + a * n, c->phiu + a * c->geo.stride, n * sizeof(float),
+                                  cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      std::memset(phiu_prev, 0, 3 * n * sizeof(float));
+    }
+  }
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (step) *step = c->step;
+  return LBM_OK;
+}
+
+lbm_status lbm_write_state(lbm_ctx* c, const float* f, const float* g, const float* phiu_prev,
+                           long long step) {
+  if (!c) return LBM_EINVAL;
+  if (!f || !g) return fail(c, LBM_EINVAL, "f and g must not be NULL");
+  if (step < 0) return fail(c, LBM_EINVAL, "step must be >= 0");
+  const size_t n = static_cast<size_t>(c->geo.n);
+  const size_t s = c->geo.stride;
+  // Even-step layout: pre-collision population q of cell x at slot (q, x).
+  for (int q = 0; q < lbm::kSlots; ++q) {
+    const float* src = q < 7 ? f + q * n : g + (q - 7) * n;
+    LBM_CK(c, cudaMemcpyAsync(c->pop + q * s, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  }
+  const bool prev = phiu_prev && step > 0;
+  if (prev)
+    for (int a = 0; a < 3; ++a)
+      LBM_CK(c, cudaMemcpyAsync(c->phiu + a * s, phiu_prev + a * n, n * sizeof(float),
+                                cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->odd = false;
+  c->have_prev = prev;
+  c->step = step;
+  c->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_step(const lbm_ctx* c, long long* step) {
+  if (!c || !step) return LBM_EINVAL;
+  *step = c->step;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_ctx* c, int enable) {
+  if (!c) return LBM_EINVAL;
+  for (auto& list : c->events) {
+    for (auto& pr : list) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    list.clear();
+  }
+  c->profiling = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* c, int kernel, double* total_ms, long long* launches) {
+  if (!c) return LBM_EINVAL;
+  if (kernel < 0 || kernel > 2 || !total_ms || !launches)
+    return fail(c, LBM_EINVAL, "kernel must be 0, 1 or 2 and outputs non-NULL");
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  double total = 0.0;
+  for (auto& pr : c->events[kernel]) {
+    float ms = 0.0f;
+    LBM_CK(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+    total += ms;
+  }
+  *total_ms = total;
+  *launches = static_cast<long long>(c->events[kernel].size());
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  release(c);
+  delete c;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

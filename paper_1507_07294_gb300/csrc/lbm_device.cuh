@@ -1,0 +1,430 @@
+// Device-side building blocks of the coupled D3Q7 + D3Q15 MRT update (Liang, Shi &
+// Chai, arXiv:1507.07294, Sec. II).  Everything here runs in FP32 on the CUDA cores:
+// the per-cell moment transforms are small, sparse and memory-bound, so they are
+// written as add trees over the orthogonal rows of M (Eq. 9) and Gamma (Eq. 25)
+// rather than as dense products.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------------
+// Parameters passed by value to every kernel (kept in the constant bank).
+// ---------------------------------------------------------------------------------
+struct Geometry {
+  int nx, ny, nz;
+  int walls;       // 1: halfway bounce-back at z = 0 and z = nz
+  int n;           // cells, < 2^31
+  int plane;       // nx * ny
+  size_t stride;   // elements between consecutive populations (= n)
+};
+
+struct Physics {
+  float rho_g;       // Eq. 14: rho = rho_g + (1 + phi) * half_drho
+  float half_drho;   // (rho_l - rho_g) / 2
+  float nu_g, half_dnu, nu_mid;  // nu(phi) = nu_mid + phi * half_dnu
+  float mob;         // mobility (Eq. 1)
+  float kappa, beta; // Eq. 2
+  float eta, A;      // Eqs. 5, 8, 19
+  float gacc[3];     // body acceleration
+  float rho_ref;     // G = (rho - rho_ref) g; 0 for the plain weight
+  float sf[7];       // S^f (Eq. 10)
+  float sg[15];      // S^g (Eq. 26), entries 9..13 unused (viscous, per cell)
+};
+
+// Population q of the D3Q7 set lives at slot q (0..6), population i of the D3Q15
+// set at slot 7 + i.  Velocity orders: Eq. 6 and Eq. 23.  In both orders the
+// opposite of i > 0 is i + 1 for odd i and i - 1 for even i.
+constexpr int kQ7 = 7;
+constexpr int kQ15 = 15;
+constexpr int kSlots = kQ7 + kQ15;
+
+// ---------------------------------------------------------------------------------
+// Neighbour offsets of one cell.  x and y wrap; z wraps or, between walls, the
+// stencil ghost of an out-of-range node is the node itself (offset 0).
+// ---------------------------------------------------------------------------------
+struct Nbr {
+  int xm, xp, ym, yp, zm, zp;  // element offsets to x-1, x+1, ...
+  bool wlo, whi;               // cell touches the bottom / top wall
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Geometry& geo, int x, int y, int z) {
+  Nbr nb;
+  nb.xm = (x == 0) ? geo.nx - 1 : -1;
+  nb.xp = (x == geo.nx - 1) ? -(geo.nx - 1) : 1;
+  nb.ym = (y == 0) ? (geo.ny - 1) * geo.nx : -geo.nx;
+  nb.yp = (y == geo.ny - 1) ? -(geo.ny - 1) * geo.nx : geo.nx;
+  if (geo.walls) {
+    nb.wlo = (z == 0);
+    nb.whi = (z == geo.nz - 1);
+    nb.zm = nb.wlo ? 0 : -geo.plane;
+    nb.zp = nb.whi ? 0 : geo.plane;
+  } else {
+    nb.wlo = nb.whi = false;
+    nb.zm = (z == 0) ? (geo.nz - 1) * geo.plane : -geo.plane;
+    nb.zp = (z == geo.nz - 1) ? -(geo.nz - 1) * geo.plane : geo.plane;
+  }
+  return nb;
+}
+
+template <int CX, int CY, int CZ>
+__device__ __forceinline__ int offset(const Nbr& nb) {
+  return (CX > 0 ? nb.xp : (CX < 0 ? nb.xm : 0)) + (CY > 0 ? nb.yp : (CY < 0 ? nb.ym : 0)) +
+         (CZ > 0 ? nb.zp : (CZ < 0 ? nb.zm : 0));
+}
+
+// ---------------------------------------------------------------------------------
+// In-place "AA" population storage (one array, no second copy).
+//
+// Even steps read population i of cell x from slot (i, x) and write the
+// post-collision value to slot (opp(i), x).  Odd steps read f_i(x) = f_i^+(x - c_i)
+// from slot (opp(i), x - c_i) and write the post-collision value to slot
+// (i, x + c_i), where the next even step finds it.  Each cell thus reads and writes
+// the same set of slots, so the update is race-free in place.  A link crossing a
+// wall is closed by bounce-back: in an odd step the read comes from slot (i, x) and
+// the write goes to slot (opp(i), x); even steps touch only their own cell.
+// ---------------------------------------------------------------------------------
+// The pointers carry no __restrict__: the fused kernel loads and then stores the same
+// slots through one array, and those loads must stay ahead of the stores.
+template <bool ODD, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+__device__ __forceinline__ float aa_load(const float* a, size_t stride, int idx,
+                                         const Nbr& nb) {
+  if (!ODD) return a[SLOT * stride + idx];
+  const bool wall = (CZ > 0 && nb.wlo) || (CZ < 0 && nb.whi);
+  if (wall) return a[SLOT * stride + idx];
+  return a[SLOT_OPP * stride + idx + offset<-CX, -CY, -CZ>(nb)];
+}
+
+template <bool ODD, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+__device__ __forceinline__ void aa_store(float* a, size_t stride, int idx,
+                                         const Nbr& nb, float v) {
+  if (!ODD) {
+    a[SLOT_OPP * stride + idx] = v;
+    return;
+  }
+  const bool wall = (CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo);
+  if (wall)
+    a[SLOT_OPP * stride + idx] = v;
+  else
+    a[SLOT * stride + idx + offset<CX, CY, CZ>(nb)] = v;
+}
+
+// D3Q7 velocities (Eq. 6) as template arguments: slot, opposite slot, c.
+#define LBM_D3Q7_LIST(X) \
+  X(0, 0, 0, 0, 0)       \
+  X(1, 2, 1, 0, 0)       \
+  X(2, 1, -1, 0, 0)      \
+  X(3, 4, 0, 1, 0)       \
+  X(4, 3, 0, -1, 0)      \
+  X(5, 6, 0, 0, 1)       \
+  X(6, 5, 0, 0, -1)
+
+// D3Q15 velocities (Eq. 23): index i, opposite, c.
+#define LBM_D3Q15_LIST(X) \
+  X(0, 0, 0, 0, 0)        \
+  X(1, 2, 1, 0, 0)        \
+  X(2, 1, -1, 0, 0)       \
+  X(3, 4, 0, 1, 0)        \
+  X(4, 3, 0, -1, 0)       \
+  X(5, 6, 0, 0, 1)        \
+  X(6, 5, 0, 0, -1)       \
+  X(7, 8, 1, 1, 1)        \
+  X(8, 7, -1, -1, -1)     \
+  X(9, 10, 1, 1, -1)      \
+  X(10, 9, -1, -1, 1)     \
+  X(11, 12, 1, -1, 1)     \
+  X(12, 11, -1, 1, -1)    \
+  X(13, 14, 1, -1, -1)    \
+  X(14, 13, -1, 1, 1)
+
+template <bool ODD>
+__device__ __forceinline__ void load_f(const float* a, size_t s, int idx,
+                                       const Nbr& nb, float f[7]) {
+#define X(I, O, CX, CY, CZ) f[I] = aa_load<ODD, I, O, CX, CY, CZ>(a, s, idx, nb);
+  LBM_D3Q7_LIST(X)
+#undef X
+}
+
+template <bool ODD>
+__device__ __forceinline__ void store_f(float* a, size_t s, int idx, const Nbr& nb,
+                                        const float f[7]) {
+#define X(I, O, CX, CY, CZ) aa_store<ODD, I, O, CX, CY, CZ>(a, s, idx, nb, f[I]);
+  LBM_D3Q7_LIST(X)
+#undef X
+}
+
+template <bool ODD>
+__device__ __forceinline__ void load_g(const float* a, size_t s, int idx,
+                                       const Nbr& nb, float g[15]) {
+#define X(I, O, CX, CY, CZ) g[I] = aa_load<ODD, 7 + I, 7 + O, CX, CY, CZ>(a, s, idx, nb);
+  LBM_D3Q15_LIST(X)
+#undef X
+}
+
+template <bool ODD>
+__device__ __forceinline__ void store_g(float* a, size_t s, int idx, const Nbr& nb,
+                                        const float g[15]) {
+#define X(I, O, CX, CY, CZ) aa_store<ODD, 7 + I, 7 + O, CX, CY, CZ>(a, s, idx, nb, g[I]);
+  LBM_D3Q15_LIST(X)
+#undef X
+}
+
+// ---------------------------------------------------------------------------------
+// Isotropic difference schemes on the 15-point D3Q15 stencil (Eqs. 35-36 with the
+// flow-lattice weights 1/9 (faces), 1/72 (corners) and c_s^2 = 1/3):
+//   grad chi = 1/3 (face differences) + 1/24 (corner differences)
+//   lap chi  = 2/3 sum_faces (chi_n - chi) + 1/12 sum_corners (chi_n - chi)
+// ---------------------------------------------------------------------------------
+struct Stencil {
+  float c;                      // centre
+  float xm, xp, ym, yp, zm, zp; // faces
+  float k[8];                   // corners, k[(sz > 0) * 4 + (sy > 0) * 2 + (sx > 0)]
+};
+
+__device__ __forceinline__ void load_stencil(const float* __restrict__ a, int idx, const Nbr& nb,
+                                             Stencil& s) {
+  s.c = __ldg(a + idx);
+  s.xm = __ldg(a + idx + nb.xm);
+  s.xp = __ldg(a + idx + nb.xp);
+  s.ym = __ldg(a + idx + nb.ym);
+  s.yp = __ldg(a + idx + nb.yp);
+  s.zm = __ldg(a + idx + nb.zm);
+  s.zp = __ldg(a + idx + nb.zp);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int ox = (b & 1) ? nb.xp : nb.xm;
+    const int oy = (b & 2) ? nb.yp : nb.ym;
+    const int oz = (b & 4) ? nb.zp : nb.zm;
+    s.k[b] = __ldg(a + idx + ox + oy + oz);
+  }
+}
+
+__device__ __forceinline__ float stencil_lap(const Stencil& s) {
+  const float faces = (s.xm + s.xp) + (s.ym + s.yp) + (s.zm + s.zp);
+  const float corners = ((s.k[0] + s.k[1]) + (s.k[2] + s.k[3])) + ((s.k[4] + s.k[5]) + (s.k[6] + s.k[7]));
+  return (2.0f / 3.0f) * (faces - 6.0f * s.c) + (1.0f / 12.0f) * (corners - 8.0f * s.c);
+}
+
+__device__ __forceinline__ void stencil_grad(const Stencil& s, float g[3]) {
+  const float kx = (s.k[1] - s.k[0]) + (s.k[3] - s.k[2]) + (s.k[5] - s.k[4]) + (s.k[7] - s.k[6]);
+  const float ky = (s.k[2] - s.k[0]) + (s.k[3] - s.k[1]) + (s.k[6] - s.k[4]) + (s.k[7] - s.k[5]);
+  const float kz = (s.k[4] - s.k[0]) + (s.k[5] - s.k[1]) + (s.k[6] - s.k[2]) + (s.k[7] - s.k[3]);
+  g[0] = (1.0f / 3.0f) * (s.xp - s.xm) + (1.0f / 24.0f) * kx;
+  g[1] = (1.0f / 3.0f) * (s.yp - s.ym) + (1.0f / 24.0f) * ky;
+  g[2] = (1.0f / 3.0f) * (s.zp - s.zm) + (1.0f / 24.0f) * kz;
+}
+
+// mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2).
+__device__ __forceinline__ float chemical_potential(const Physics& ph, float phi, float lap_phi) {
+  return 4.0f * ph.beta * phi * (phi * phi - 1.0f) - ph.kappa * lap_phi;
+}
+
+// ---------------------------------------------------------------------------------
+// Macroscopic state of one cell from its D3Q15 populations and the stencils.
+// ---------------------------------------------------------------------------------
+struct Macro {
+  float rho, p;
+  float u[3];
+  float grad_rho[3];
+  float F[3];  // F_s + F_a + G
+};
+
+// Eqs. 14, 29, 30 and the forces of Eq. 28.
+__device__ __forceinline__ Macro macroscopic(const Physics& ph, const float g[15], float phi,
+                                             float mu, const float grad_phi[3], float lap_mu) {
+  Macro m;
+  m.rho = ph.rho_g + (1.0f + phi) * ph.half_drho;
+  // lattice momentum sum_i c_i g_i and sum_{i != 0} g_i
+  const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12], d13 = g[13] - g[14];
+  const float jx = (g[1] - g[2]) + ((d7 + d9) + (d11 + d13));
+  const float jy = (g[3] - g[4]) + ((d7 + d9) - (d11 + d13));
+  const float jz = (g[5] - g[6]) + ((d7 - d9) + (d11 - d13));
+  const float sum_moving = ((g[1] + g[2]) + (g[3] + g[4]) + (g[5] + g[6])) +
+                           (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14])));
+  float Fsg[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    m.grad_rho[a] = ph.half_drho * grad_phi[a];
+    Fsg[a] = mu * grad_phi[a] + (m.rho - ph.rho_ref) * ph.gacc[a];  // F_s + G
+  }
+  const float fa = ph.half_drho * ph.mob * lap_mu;  // F_a = fa * u
+  const float inv = 1.0f / (m.rho - 0.5f * fa);
+  m.u[0] = (jx + 0.5f * Fsg[0]) * inv;
+  m.u[1] = (jy + 0.5f * Fsg[1]) * inv;
+  m.u[2] = (jz + 0.5f * Fsg[2]) * inv;
+  const float uu = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
+  const float udr = m.u[0] * m.grad_rho[0] + m.u[1] * m.grad_rho[1] + m.u[2] * m.grad_rho[2];
+  // c_s^2/(1 - omega_0) = 3/7; rho s_0(u) = -rho u^2 / 3
+  m.p = (3.0f / 7.0f) * (sum_moving + 0.5f * udr - m.rho * uu * (1.0f / 3.0f));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) m.F[a] = Fsg[a] + fa * m.u[a];
+  return m;
+}
+
+// ---------------------------------------------------------------------------------
+// D3Q15 MRT collision in moment space (Eqs. 20, 26, 31, 32):
+//   m+ = m - S (m - m^eq) + (I - S/2) mT,   g+ = Gamma^{-1} m+
+// written as g+ = g - Gamma^{-1} Delta with Delta = S (m - m^eq) - (I - S/2) mT, so
+// that the small correction is what passes through the FP32 back-transform.
+// Gamma^{-1} = Gamma^T diag(1/|row_k|^2), |row|^2 = 15,18,360,10,40,10,40,10,40,12,4,8,8,8,8.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], const Macro& M,
+                                              float lambda_visc) {
+  // forward transform (rows as polynomials of c; see Eq. 25)
+  const float sx = g[1] + g[2], dx = g[1] - g[2];
+  const float sy = g[3] + g[4], dy = g[3] - g[4];
+  const float sz = g[5] + g[6], dz = g[5] - g[6];
+  const float s7 = g[7] + g[8], d7 = g[7] - g[8];     // +-(1, 1, 1)
+  const float s9 = g[9] + g[10], d9 = g[9] - g[10];   // +-(1, 1,-1)
+  const float s11 = g[11] + g[12], d11 = g[11] - g[12]; // +-(1,-1, 1)
+  const float s13 = g[13] + g[14], d13 = g[13] - g[14]; // +-(1,-1,-1)
+  const float sa = sx + sy + sz;
+  const float C = (s7 + s9) + (s11 + s13);
+  const float Cx = (d7 + d9) + (d11 + d13);
+  const float Cy = (d7 + d9) - (d11 + d13);
+  const float Cz = (d7 - d9) + (d11 - d13);
+  float m[15];
+  m[0] = g[0] + sa + C;
+  m[1] = -2.0f * g[0] - sa + C;
+  m[2] = 16.0f * g[0] - 4.0f * sa + C;
+  m[3] = dx + Cx;
+  m[4] = -4.0f * dx + Cx;
+  m[5] = dy + Cy;
+  m[6] = -4.0f * dy + Cy;
+  m[7] = dz + Cz;
+  m[8] = -4.0f * dz + Cz;
+  m[9] = 2.0f * sx - sy - sz;
+  m[10] = sy - sz;
+  m[11] = (s7 + s9) - (s11 + s13);
+  m[12] = (s7 - s9) - (s11 - s13);
+  m[13] = (s7 - s9) + (s11 - s13);
+  m[14] = (d7 - d9) - (d11 - d13);
+
+  // equilibrium moments, Eq. 31 (c = 1)
+  const float rho = M.rho, p = M.p, ux = M.u[0], uy = M.u[1], uz = M.u[2];
+  const float uu = ux * ux + uy * uy + uz * uz;
+  float meq[15];
+  meq[0] = 0.0f;
+  meq[1] = 3.0f * p + rho * uu;
+  meq[2] = -(45.0f * p + 5.0f * rho * uu);
+  meq[3] = rho * ux;
+  meq[4] = (-7.0f / 3.0f) * rho * ux;
+  meq[5] = rho * uy;
+  meq[6] = (-7.0f / 3.0f) * rho * uy;
+  meq[7] = rho * uz;
+  meq[8] = (-7.0f / 3.0f) * rho * uz;
+  meq[9] = rho * (2.0f * ux * ux - uy * uy - uz * uz);
+  meq[10] = rho * (uy * uy - uz * uz);
+  meq[11] = rho * ux * uy;
+  meq[12] = rho * uy * uz;
+  meq[13] = rho * ux * uz;
+  meq[14] = 0.0f;
+
+  // forcing moments, Eq. 32 (c = 1, X = c_s^2 grad rho)
+  const float Xx = M.grad_rho[0] * (1.0f / 3.0f), Xy = M.grad_rho[1] * (1.0f / 3.0f),
+              Xz = M.grad_rho[2] * (1.0f / 3.0f);
+  const float Fx = M.F[0], Fy = M.F[1], Fz = M.F[2];
+  const float Yx = Xx + Fx, Yy = Xy + Fy, Yz = Xz + Fz;
+  const float udX = ux * Xx + uy * Xy + uz * Xz;
+  const float udF = ux * Fx + uy * Fy + uz * Fz;
+  float mT[15];
+  mT[0] = 3.0f * udX;  // u . grad rho
+  mT[1] = -udX + 2.0f * udF;
+  mT[2] = -(7.0f * udX + 10.0f * udF);
+  mT[3] = Fx;
+  mT[4] = (-7.0f / 3.0f) * Fx;
+  mT[5] = Fy;
+  mT[6] = (-7.0f / 3.0f) * Fy;
+  mT[7] = Fz;
+  mT[8] = (-7.0f / 3.0f) * Fz;
+  mT[9] = 4.0f * ux * Yx - 2.0f * uy * Yy - 2.0f * uz * Yz;
+  mT[10] = 2.0f * uy * Yy - 2.0f * uz * Yz;
+  mT[11] = ux * Yy + uy * Yx;
+  mT[12] = uy * Yz + uz * Yy;
+  mT[13] = ux * Yz + uz * Yx;
+  mT[14] = 0.0f;
+
+  // Delta_k / |row_k|^2
+  constexpr float inv_n[15] = {1.0f / 15, 1.0f / 18, 1.0f / 360, 1.0f / 10, 1.0f / 40,
+                               1.0f / 10, 1.0f / 40,  1.0f / 10, 1.0f / 40, 1.0f / 12,
+                               1.0f / 4,  1.0f / 8,   1.0f / 8,  1.0f / 8,  1.0f / 8};
+  float a[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) {
+    const float lam = (k >= 9 && k <= 13) ? lambda_visc : ph.sg[k];
+    a[k] = (lam * (m[k] - meq[k]) - (1.0f - 0.5f * lam) * mT[k]) * inv_n[k];
+  }
+
+  // back transform: g_i -= sum_k Gamma_ki a_k
+  const float e_axis = a[0] - a[1] - 4.0f * a[2];
+  g[0] -= a[0] - 2.0f * a[1] + 16.0f * a[2];
+  {
+    const float ox = a[3] - 4.0f * a[4], ex = e_axis + 2.0f * a[9];
+    g[1] -= ex + ox;
+    g[2] -= ex - ox;
+    const float oy = a[5] - 4.0f * a[6], ey = e_axis - a[9] + a[10];
+    g[3] -= ey + oy;
+    g[4] -= ey - oy;
+    const float oz = a[7] - 4.0f * a[8], ez = e_axis - a[9] - a[10];
+    g[5] -= ez + oz;
+    g[6] -= ez - oz;
+  }
+  {
+    const float e0 = a[0] + a[1] + a[2];
+    const float px = a[3] + a[4], py = a[5] + a[6], pz = a[7] + a[8];
+    // corner v = (vx, vy, vz): even part e0 + vx vy a11 + vy vz a12 + vx vz a13,
+    // odd part vx px + vy py + vz pz + vx vy vz a14; g(+v) -= even + odd, g(-v) -= even - odd
+    float e, o;
+    e = e0 + a[11] + a[12] + a[13]; o = px + py + pz + a[14];   // (1, 1, 1)
+    g[7] -= e + o; g[8] -= e - o;
+    e = e0 + a[11] - a[12] - a[13]; o = px + py - pz - a[14];   // (1, 1,-1)
+    g[9] -= e + o; g[10] -= e - o;
+    e = e0 - a[11] - a[12] + a[13]; o = px - py + pz - a[14];   // (1,-1, 1)
+    g[11] -= e + o; g[12] -= e - o;
+    e = e0 - a[11] + a[12] - a[13]; o = px - py - pz + a[14];   // (1,-1,-1)
+    g[13] -= e + o; g[14] -= e - o;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// D3Q7 MRT collision in moment space (Eqs. 15, 17, 18):
+//   m+ = m - S (m - m^eq) + (I - S/2) mR,   f+ = M^{-1} m+
+// again applied as f+ = f - M^{-1} Delta; |row|^2 of M = 7, 2, 2, 2, 42, 12, 4.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], float phi, float mu,
+                                             const float u[3], const float dphiu[3]) {
+  const float sx = f[1] + f[2], sy = f[3] + f[4], sz = f[5] + f[6];
+  float m[7];
+  m[0] = f[0] + (sx + sy + sz);
+  m[1] = f[1] - f[2];
+  m[2] = f[3] - f[4];
+  m[3] = f[5] - f[6];
+  m[4] = 6.0f * f[0] - (sx + sy + sz);
+  m[5] = 2.0f * sx - sy - sz;
+  m[6] = sy - sz;
+  const float meq[7] = {phi, phi * u[0], phi * u[1], phi * u[2],
+                        6.0f * phi - 21.0f * ph.A * ph.eta * mu, 0.0f, 0.0f};
+  const float mR[7] = {0.0f, dphiu[0], dphiu[1], dphiu[2], 0.0f, 0.0f, 0.0f};
+  constexpr float inv_n[7] = {1.0f / 7, 1.0f / 2, 1.0f / 2, 1.0f / 2, 1.0f / 42, 1.0f / 12, 1.0f / 4};
+  float b[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const float s = ph.sf[k];
+    b[k] = (s * (m[k] - meq[k]) - (1.0f - 0.5f * s) * mR[k]) * inv_n[k];
+  }
+  const float e = b[0] - b[4];
+  f[0] -= b[0] + 6.0f * b[4];
+  const float ex = e + 2.0f * b[5];
+  f[1] -= ex + b[1];
+  f[2] -= ex - b[1];
+  const float ey = e - b[5] + b[6];
+  f[3] -= ey + b[2];
+  f[4] -= ey - b[2];
+  const float ez = e - b[5] - b[6];
+  f[5] -= ez + b[3];
+  f[6] -= ez - b[3];
+}
+
+}  // namespace lbm

@@ -1,0 +1,93 @@
+"""The C ABI library builds, loads and exports every entry point of include/lbm.h, and
+its host-side argument validation works without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1507_07294_gb300 import lbm as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return L.load_library()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_init_phi", "lbm_step", "lbm_read_fields", "lbm_reduce",
+                     "lbm_destroy", "lbm_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(L._SIGNATURES)
+
+
+def _create(lib, grid, params, alloc=None):
+    out = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(grid), ctypes.byref(params), alloc, None, ctypes.byref(out))
+    return st, out
+
+
+def _good():
+    grid = L.LbmGrid(8, 8, 8, 0)
+    params = L.make_params(3.0, 1.0, 0.1, 0.1, 0.1, 4.0, 0.01)
+    return grid, params
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    (lambda g, p: setattr(g, "nx", 0), "grid sizes"),
+    (lambda g, p: setattr(g, "walls_z", 2), "walls_z"),
+    (lambda g, p: setattr(p, "rho_g", 0.0), "densities"),
+    (lambda g, p: setattr(p, "nu_l", -1.0), "viscosities"),
+    (lambda g, p: setattr(p, "A", 0.4), "A must"),
+    (lambda g, p: p.sf.__setitem__(4, 2.0), "sf rates"),
+    (lambda g, p: p.sf.__setitem__(2, 1.3), "s_1 = s_2 = s_3"),
+    (lambda g, p: p.sg.__setitem__(0, 0.0), "sg rates"),
+    (lambda g, p: setattr(p, "storage", 7), "storage"),
+    (lambda g, p: (setattr(g, "nx", 2048), setattr(g, "ny", 1024), setattr(g, "nz", 1024)), "2^31"),
+])
+def test_create_rejects_bad_arguments(lib, mutate, expect):
+    grid, params = _good()
+    mutate(grid, params)
+    st, out = _create(lib, grid, params)
+    assert st == L.LBM_EINVAL
+    assert out.value is None
+    assert expect in lib.lbm_last_error(None).decode()
+
+
+def test_viscous_rates_are_not_validated(lib):
+    """lambda_9..13 come from nu(phi), so their input values are ignored."""
+    grid, params = _good()
+    params.sg[10] = 5.0
+    grid.nx = 0  # still fails, but for the grid, not for sg[10]
+    st, _ = _create(lib, grid, params)
+    assert st == L.LBM_EINVAL
+    assert "grid" in lib.lbm_last_error(None).decode()
+
+
+def test_null_arguments(lib):
+    grid, params = _good()
+    assert lib.lbm_create(ctypes.byref(grid), ctypes.byref(params), None, None, None) == L.LBM_EINVAL
+    assert lib.lbm_step(None, 1) == L.LBM_EINVAL
+    assert lib.lbm_destroy(None) == L.LBM_EINVAL
+    assert lib.lbm_init_phi(None, None, None, None) == L.LBM_EINVAL

@@ -1,0 +1,250 @@
+"""CUDA path vs FP64 oracle, through the C ABI (needs a GPU).
+
+Tolerances (FP32 arithmetic and storage against FP64): after 100 steps
+max|phi_gpu - phi_oracle| <= 1e-5 and max|u_gpu - u_oracle| / U <= 1e-4, U the
+problem's velocity scale; one step from a common state agrees to a few FP32 ulps of
+the population magnitudes.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm_oracle as O
+from paper_1507_07294_gb300 import inputs as I
+from tests.patch_oracle import one_step_at, sample_cells
+
+pytestmark = pytest.mark.gpu
+
+PHI_TOL = 1e-5
+U_TOL_REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1507_07294_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
+def _oracle(w):
+    o = O.Oracle(O.Params.from_workload(w))
+    o.init(w.phi0, w.u0, w.p0)
+    return o
+
+
+def _compare_fields(gf, of, U, phi_tol=PHI_TOL, u_tol=U_TOL_REL, p_tol=None):
+    dphi = np.abs(gf["phi"] - of["phi"]).max()
+    du = np.abs(gf["u"] - of["u"]).max() / U
+    assert dphi <= phi_tol, f"max|dphi| = {dphi:.3e}"
+    assert du <= u_tol, f"max|du|/U = {du:.3e}"
+    if p_tol is not None:
+        dp = np.abs(gf["p"] - of["p"]).max()
+        assert dp <= p_tol, f"max|dp| = {dp:.3e}"
+    np.testing.assert_allclose(gf["rho"], of["rho"], atol=1e-5)
+    return dphi, du
+
+
+def test_initial_fields(L):
+    w = I.perturbed(I.droplet(n=16, R=5.0, nx=20, ny=18, nz=16), seed=1, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w) as s:
+        gf = s.fields()
+    of = _oracle(w).fields()
+    _compare_fields(gf, of, w.U, phi_tol=1e-6, u_tol=1e-5, p_tol=1e-7)
+    np.testing.assert_allclose(gf["mu"], of["mu"], atol=1e-7)
+
+
+def test_droplet_100_steps(L):
+    """The static droplet (32^3, R = 8, D = 4, sigma = 0.01, rho 3:1, nu = 0.1,
+    Mob = 0.1), seeded velocity and pressure noise so every term acts."""
+    w = I.perturbed(I.droplet(n=32, R=8.0), seed=0, u_amp=0.005, p_amp=1e-4)
+    with L.Solver(w) as s:
+        s.step(100)
+        gf = s.fields()
+        assert s.t == 100
+    o = _oracle(w)
+    o.step(100)
+    _compare_fields(gf, o.fields(), w.U, p_tol=1e-6)
+
+
+def test_rayleigh_taylor_ragged_100_steps(L):
+    """Walls in z, gravity, ragged sizes in all three directions (not multiples of a
+    block or a warp)."""
+    w = I.rayleigh_taylor(W=37, nz=70, Re=256.0)
+    w.ny = 29
+    w.phi0 = np.ascontiguousarray(w.phi0[:, :29, :])
+    w = I.perturbed(w, seed=2, u_amp=0.01, p_amp=1e-4)
+    with L.Solver(w) as s:
+        s.step(100)
+        gf = s.fields()
+    o = _oracle(w)
+    o.step(100)
+    _compare_fields(gf, o.fields(), w.U, p_tol=1e-6)
+
+
+def test_every_term_and_option(L):
+    """Unequal relaxation rates in both lattices, unequal viscosities, gravity along
+    all axes in the buoyancy form, A != 1/4: 40 steps."""
+    w = I.perturbed(I.droplet(n=14, R=4.0, nx=17, ny=14, nz=13, nu=0.05), seed=3,
+                    phi_amp=0.05, u_amp=0.01, p_amp=1e-3)
+    w.nu_g = 0.2
+    w.g = (2e-5, -1e-5, 3e-5)
+    w.buoyancy = True
+    w.A = 0.2
+    w.sf = (1.1, 1.4, 1.4, 1.4, 1.3, 0.8, 1.6)
+    w.sg = (1.0, 1.2, 0.9, 1.1, 1.3, 1.1, 1.3, 1.1, 1.3, 1.0, 1.0, 1.0, 1.0, 1.0, 1.5)
+    with L.Solver(w) as s:
+        s.step(40)
+        gf = s.fields()
+    o = _oracle(w)
+    o.step(40)
+    _compare_fields(gf, o.fields(), 0.01, p_tol=1e-6)
+
+
+@pytest.mark.parametrize("shape,walls", [((1, 1, 1), False), ((1, 5, 7), False), ((3, 1, 4), True),
+                                         ((1, 2, 3), True), ((5, 3, 2), False), ((9, 33, 1), True)])
+def test_degenerate_grids(L, shape, walls):
+    """Grids one cell thick in some direction, a single cell, walls one cell apart."""
+    nz, ny, nx = shape
+    w = I.droplet(n=4, R=1.5, nx=nx, ny=ny, nz=nz)
+    w.walls_z = walls
+    w = I.perturbed(w, seed=4, phi_amp=0.3, u_amp=0.01, p_amp=1e-3)
+    w.g = (1e-5, 0.0, -2e-5)
+    with L.Solver(w) as s:
+        s.step(20)
+        gf = s.fields()
+    o = _oracle(w)
+    o.step(20)
+    _compare_fields(gf, o.fields(), 0.01)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_state_after_one_and_two_steps(L, walls):
+    """Raw populations against the oracle after one (odd layout) and two (even layout)
+    steps: within a few FP32 ulps of the population magnitudes."""
+    if walls:
+        w = I.perturbed(I.rayleigh_taylor(W=12, nz=20, Re=100.0), seed=5, u_amp=0.02, p_amp=1e-3)
+    else:
+        w = I.perturbed(I.droplet(n=12, R=4.0, nx=13, ny=12, nz=11), seed=5, u_amp=0.02, p_amp=1e-3)
+    o = _oracle(w)
+    with L.Solver(w) as s:
+        for k in (1, 2):
+            s.step(1)
+            o.step(1)
+            f, g, phiu, t = s.state()
+            assert t == k
+            np.testing.assert_allclose(f, o.f, atol=2e-6 * np.abs(o.f).max())
+            np.testing.assert_allclose(g, o.g, atol=2e-6 * np.abs(o.g).max())
+            np.testing.assert_allclose(phiu, o.phiu_prev, atol=1e-7)
+
+
+def _sampled_one_step(L, w, warm_steps, n_samples, seed):
+    """Run warm_steps on the GPU, take its state, advance one more step on the GPU and,
+    at sampled cells, with the oracle from the same state."""
+    p = O.Params.from_workload(w)
+    with L.Solver(w) as s:
+        s.step(warm_steps)
+        f, g, phiu, _ = s.state()
+        s.step(1)
+        f1, g1, _, _ = s.state()
+    cells = sample_cells(w.shape, n_samples, seed=seed)
+    of, og = one_step_at(p, f, g, phiu, warm_steps > 0, cells)
+    idx = tuple(np.array(cells).T)
+    gf = np.moveaxis(f1[(slice(None),) + idx], 0, 1)
+    gg = np.moveaxis(g1[(slice(None),) + idx], 0, 1)
+    np.testing.assert_allclose(gf, of, atol=2e-6 * max(1.0, np.abs(of).max()))
+    np.testing.assert_allclose(gg, og, atol=2e-6 * np.abs(og).max() + 1e-9)
+
+
+def test_full_size_rayleigh_taylor_64(L):
+    """Coupled Rayleigh-Taylor at its full size (64 x 64 x 256, Re = 256, At = 0.5):
+    one step at 200 sampled cells (plus the box corners) after 99 GPU steps."""
+    w = I.rayleigh_taylor(W=64, Re=256.0)
+    _sampled_one_step(L, w, 99, 200, seed=7)
+
+
+def test_full_size_rayleigh_taylor_256(L):
+    """Rayleigh-Taylor at Re = 4000 on 256 x 256 x 1024 (67M cells), the benchmarked
+    configuration: one step at 100 sampled cells after 9 GPU steps."""
+    w = I.rayleigh_taylor(W=256, Re=4000.0)
+    _sampled_one_step(L, w, 9, 100, seed=8)
+
+
+def test_mass_conservation(L):
+    """sum phi (FP64 device reduction) drifts only by FP32 rounding over 500 steps."""
+    w = I.perturbed(I.rayleigh_taylor(W=32, nz=96, Re=256.0), seed=9, u_amp=0.01)
+    with L.Solver(w) as s:
+        s0, _ = s.reduce()
+        s.step(500)
+        s1, _ = s.reduce()
+    assert abs(s1 - s0) <= 1e-6 * np.abs(w.phi0).sum()
+
+
+def test_reduce_matches_oracle(L):
+    w = I.perturbed(I.droplet(n=16, R=5.0, nx=19, ny=16, nz=15), seed=10, u_amp=0.01, p_amp=1e-3)
+    o = _oracle(w)
+    with L.Solver(w) as s:
+        s.step(7)
+        sp, mom = s.reduce()
+    o.step(7)
+    osp, omom = o.totals()
+    assert abs(sp - osp) <= 1e-5 * np.abs(w.phi0).sum() / w.cells * 10 + 1e-4
+    np.testing.assert_allclose(mom, omom, atol=1e-6 * w.cells * 1e-2)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_resume_is_bit_exact(L, k):
+    """Read the state after k steps (odd and even layouts), continue 5 steps; a fresh
+    context resumed from that state gives the same populations bit for bit."""
+    w = I.perturbed(I.rayleigh_taylor(W=16, nz=24, Re=100.0), seed=11, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w) as a:
+        a.step(k)
+        st = a.state()
+        a.step(5)
+        ref = a.state()
+    with L.Solver(w, init=False) as b:
+        b.set_state(st[0], st[1], st[2], st[3])
+        assert b.t == k
+        b.step(5)
+        got = b.state()
+    for x, y in zip(ref[:3], got[:3]):
+        assert np.array_equal(x, y)
+    assert ref[3] == got[3] == k + 5
+
+
+def test_zero_steps_changes_nothing(L):
+    w = I.droplet(n=8, R=2.5)
+    with L.Solver(w) as s:
+        before = s.state()
+        s.step(0)
+        after = s.state()
+    for x, y in zip(before[:3], after[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_non_finite_state_is_reported(L):
+    """A NaN in the initial condition surfaces as LBM_EUNSTABLE from lbm_reduce."""
+    w = I.droplet(n=8, R=2.5)
+    w.phi0 = w.phi0.copy()
+    w.phi0[3, 4, 5] = np.nan
+    with L.Solver(w) as s:
+        s.step(2)
+        _, _, st = L.lbm_reduce(s.ctx, check=False)
+    assert st == L.LBM_EUNSTABLE
+
+
+def test_step_before_init_is_rejected(L):
+    w = I.droplet(n=8, R=2.5)
+    with L.Solver(w, init=False) as s:
+        with pytest.raises(L.LbmError) as e:
+            s.step(1)
+        assert e.value.status == L.LBM_EINVAL
+
+
+def test_profile_counts_launches(L):
+    w = I.droplet(n=16, R=5.0)
+    with L.Solver(w) as s:
+        L.lbm_profile(s.ctx, True)
+        s.step(6)
+        for k in range(3):
+            ms, n = L.lbm_profile_read(s.ctx, k)
+            assert n == 6 and ms > 0
+        L.lbm_profile(s.ctx, False)
