@@ -192,7 +192,7 @@ def config_dict(args, w, world):
     spec = WORKLOADS[args.workload]
     return {"workload": f"{args.workload}: {spec['desc']}",
             "grid": [w.nx, w.ny, w.nz], "cells": w.cells, "walls_z": bool(w.walls_z),
-            "storage": "fp32", "aa_in_place_streaming": True,
+            "storage": "fp32", "pattern": getattr(args, "pattern", "ab"),
             "l2": f"state {w.cells * 100 / 1e9:.1f} GB (f, g, phi u) > 129 MB L2: no flush needed",
             "parallelism": f"replicas x{world} (independent runs per GPU)"}
 
@@ -248,7 +248,7 @@ def run_ours(args):
     spec = WORKLOADS[args.workload]
     w = I.rayleigh_taylor(W=spec["W"], Re=spec["Re"])
     stream = torch.cuda.current_stream()
-    solver = L.Solver(w, stream=stream.cuda_stream)
+    solver = L.Solver(w, stream=stream.cuda_stream, pattern=args.pattern)
     ctx = solver.ctx
 
     def barrier():
@@ -353,6 +353,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rt256")
+    ap.add_argument("--pattern", choices=("ab", "aa"), default="ab",
+                    help="population storage: two arrays (ab) or in place (aa)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

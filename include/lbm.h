@@ -60,6 +60,15 @@ typedef struct {
 /* Storage types for lbm_params.storage. */
 #define LBM_STORAGE_FP32 0
 
+/* Population storage patterns for lbm_params.pattern.
+ * LBM_PATTERN_AB: two arrays; each step pulls from one and writes the other (176
+ *   bytes of populations per cell).  The faster of the two on GB300.
+ * LBM_PATTERN_AA: one array updated in place (88 bytes of populations per cell);
+ *   alternate steps read and write neighbouring cells' slots, which moves data more
+ *   slowly than LBM_PATTERN_AB.  Same results either way, bit for bit. */
+#define LBM_PATTERN_AB 0
+#define LBM_PATTERN_AA 1
+
 /* Physical and lattice parameters (the problem statement of Sec. II). */
 typedef struct {
   double rho_l, rho_g; /* phase densities; rho(phi) by Eq. 14, phi = +1 is rho_l      */
@@ -76,6 +85,7 @@ typedef struct {
                           lambda_9..13 are ignored: they follow nu(phi)              */
   unsigned flags;      /* LBM_FLAG_*                                                  */
   int storage;         /* LBM_STORAGE_FP32                                            */
+  int pattern;         /* LBM_PATTERN_AB (default, 0) or LBM_PATTERN_AA               */
 } lbm_params;
 
 /* Device allocator.  alloc returns device memory of at least `bytes` bytes (aligned
@@ -97,9 +107,10 @@ typedef struct {
 /* Create a solver for `grid` and `params`.  `alloc` may be NULL (cudaMalloc is then
  * used); `cuda_stream` is a cudaStream_t or NULL.  Fails with LBM_EINVAL when a size
  * is < 1, N >= 2^31, a rate is outside (0, 2), s_1..3 differ, A is outside (0, 1/3),
- * a density or viscosity is not positive, or the storage type is unknown.
- * Device memory: 22 populations + phi u (3) + phi + mu + 5 staging floats per cell,
- * i.e. 128 bytes per cell in FP32. */
+ * a density or viscosity is not positive, or the storage type or pattern is unknown.
+ * Device memory per cell (FP32): the cell state (22 populations + phi u of the
+ * previous step, 100 bytes; twice for LBM_PATTERN_AB) + phi + mu + 5 staging floats,
+ * i.e. 228 bytes (AB) or 128 bytes (AA). */
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
                       const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out);
 

@@ -23,8 +23,8 @@ struct lbm_ctx {
   cudaStream_t stream = nullptr;
 
   // device memory
-  float* pop = nullptr;    // 22 populations, AA layout, stride geo.stride
-  float* phiu = nullptr;   // phi u of the previous step, 3 planes
+  float* pop[2] = {nullptr, nullptr};  // tiled cell state(s): 22 populations + phi u
+  int cur = 0;             // array holding the current state (pattern AB)
   float* phi = nullptr;    // order parameter of the current step
   float* mu = nullptr;     // chemical potential of the current step
   float* stage = nullptr;  // 5 planes: field read-out, state gather, init inputs
@@ -32,7 +32,7 @@ struct lbm_ctx {
   double* red = nullptr;      // 5 reduction results
 
   long long step = 0;
-  bool odd = false;        // AA parity of the stored populations
+  bool odd = false;        // parity of the stored populations (pattern AA)
   bool have_prev = false;  // phiu holds the previous step's phi u
   bool initialized = false;
 
@@ -81,6 +81,14 @@ void dev_free(lbm_ctx* c, void* p) {
 
 bool rate_ok(double s) { return s > 0.0 && s < 2.0 && std::isfinite(s); }
 
+// Multiplier and shift of the multiply-shift division by d (see lbm::FastDiv).
+lbm::FastDiv make_fast_div(unsigned d) {
+  unsigned l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return lbm::FastDiv{d, static_cast<unsigned>(m), l};
+}
+
 // Float copies of the derived parameters (Eqs. 2, 14, 19, 33).
 lbm::Physics make_physics(const lbm_params& p) {
   lbm::Physics ph{};
@@ -124,6 +132,8 @@ lbm_status validate(const lbm_grid* g, const lbm_params* p) {
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->g[a])) return fail(nullptr, LBM_EINVAL, "g must be finite");
   if (p->storage != LBM_STORAGE_FP32) return fail(nullptr, LBM_EINVAL, "unknown storage type");
+  if (p->pattern != LBM_PATTERN_AB && p->pattern != LBM_PATTERN_AA)
+    return fail(nullptr, LBM_EINVAL, "unknown population pattern");
   return LBM_OK;
 }
 
@@ -133,16 +143,24 @@ void release(lbm_ctx* c) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
     }
-  dev_free(c, c->pop);
-  dev_free(c, c->phiu);
+  dev_free(c, c->pop[0]);
+  dev_free(c, c->pop[1]);
   dev_free(c, c->phi);
   dev_free(c, c->mu);
   dev_free(c, c->stage);
   dev_free(c, c->partial);
   dev_free(c, c->red);
-  c->pop = c->phiu = c->phi = c->mu = c->stage = nullptr;
+  c->pop[0] = c->pop[1] = c->phi = c->mu = c->stage = nullptr;
   c->partial = c->red = nullptr;
 }
+
+// Pattern of the next step's reads of the current state.
+int read_pattern(const lbm_ctx* c) {
+  if (c->params.pattern == LBM_PATTERN_AB) return lbm::kAB;
+  return c->odd ? lbm::kAAOdd : lbm::kAAEven;
+}
+
+float* cur_state(lbm_ctx* c) { return c->pop[c->cur]; }
 
 template <typename F>
 cudaError_t timed(lbm_ctx* c, int kernel, F&& launch) {
@@ -198,23 +216,27 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   c->geo.n = static_cast<int>(n);
   c->geo.plane = grid->nx * grid->ny;
   c->geo.stride = static_cast<size_t>((n + 63) / 64 * 64);  // 256-byte aligned planes
+  c->geo.div_nx = make_fast_div(static_cast<unsigned>(grid->nx));
+  c->geo.div_ny = make_fast_div(static_cast<unsigned>(grid->ny));
   c->ph = make_physics(*params);
 
   const size_t plane = c->geo.stride * sizeof(float);
-  c->pop = static_cast<float*>(dev_alloc(c, plane * lbm::kSlots));
-  c->phiu = static_cast<float*>(dev_alloc(c, plane * 3));
+  const size_t state_bytes = lbm::state_floats(c->geo.n) * sizeof(float);
+  c->pop[0] = static_cast<float*>(dev_alloc(c, state_bytes));
+  if (params->pattern == LBM_PATTERN_AB) c->pop[1] = static_cast<float*>(dev_alloc(c, state_bytes));
   c->phi = static_cast<float*>(dev_alloc(c, plane));
   c->mu = static_cast<float*>(dev_alloc(c, plane));
   c->stage = static_cast<float*>(dev_alloc(c, plane * 5));
   c->partial = static_cast<double*>(dev_alloc(c, sizeof(double) * 5 * lbm::kReduceMaxParts));
   c->red = static_cast<double*>(dev_alloc(c, sizeof(double) * 8));
-  if (!c->pop || !c->phiu || !c->phi || !c->mu || !c->stage || !c->partial || !c->red) {
+  if (!c->pop[0] || (params->pattern == LBM_PATTERN_AB && !c->pop[1]) || !c->phi || !c->mu ||
+      !c->stage || !c->partial || !c->red) {
     release(c);
     delete c;
     return fail(nullptr, LBM_ENOMEM, "device allocation failed");
   }
-  cudaError_t e = cudaMemsetAsync(c->pop, 0, plane * lbm::kSlots, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->phiu, 0, plane * 3, c->stream);
+  cudaError_t e = cudaMemsetAsync(c->pop[0], 0, state_bytes, c->stream);
+  if (e == cudaSuccess && c->pop[1]) e = cudaMemsetAsync(c->pop[1], 0, state_bytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     release(c);
@@ -242,15 +264,16 @@ lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const do
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = upload(u + a * n, c->stage + a * s);
   if (e == cudaSuccess && p) e = upload(p, c->stage + 3 * s);
   if (e == cudaSuccess) e = lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream);
+  c->cur = 0;
+  c->odd = false;
   if (e == cudaSuccess)
-    e = lbm::launch_init(c->pop, c->phiu, c->phi, c->mu, u ? c->stage : nullptr,
-                         p ? c->stage + 3 * s : nullptr, c->geo, c->ph, c->stream);
+    e = lbm::launch_init(cur_state(c), c->phi, c->mu, u ? c->stage : nullptr,
+                         p ? c->stage + 3 * s : nullptr, c->geo, c->ph, read_pattern(c), c->stream);
   const cudaError_t es = cudaStreamSynchronize(c->stream);
   dev_free(c, tmp);
   if (e != cudaSuccess) return fail_cuda(c, "lbm_init_phi", e);
   if (es != cudaSuccess) return fail_cuda(c, "lbm_init_phi", es);
   c->step = 0;
-  c->odd = false;
   c->have_prev = false;
   c->initialized = true;
   return LBM_OK;
@@ -261,15 +284,20 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
   for (int it = 0; it < n; ++it) {
-    const bool odd = c->odd;
-    LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(c->pop, c->phi, c->geo, odd, c->stream); }));
+    const int pat = read_pattern(c);
+    const float* src = cur_state(c);
+    float* dst = c->params.pattern == LBM_PATTERN_AB ? c->pop[1 - c->cur] : c->pop[c->cur];
+    LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->geo, pat, c->stream); }));
     LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
     const bool prev = c->have_prev;
     LBM_CK(c, timed(c, 2, [&] {
-             return lbm::launch_collide(c->pop, c->phiu, c->phi, c->mu, c->geo, c->ph, odd, prev,
+             return lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev,
                                         c->stream);
            }));
-    c->odd = !c->odd;
+    if (c->params.pattern == LBM_PATTERN_AB)
+      c->cur = 1 - c->cur;
+    else
+      c->odd = !c->odd;
     c->have_prev = true;
     ++c->step;
   }
@@ -283,10 +311,11 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   if (((mask & LBM_FIELD_PHI) && !phi) || ((mask & LBM_FIELD_RHO) && !rho) ||
       ((mask & LBM_FIELD_P) && !p) || ((mask & LBM_FIELD_U) && !u) || ((mask & LBM_FIELD_MU) && !mu))
     return fail(c, LBM_EINVAL, "a selected field has a NULL buffer");
-  LBM_CK(c, lbm::launch_phi(c->pop, c->phi, c->geo, c->odd, c->stream));
+  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, c->geo, read_pattern(c), c->stream));
   LBM_CK(c, lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream));
   if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
-    LBM_CK(c, lbm::launch_fields(c->pop, c->phi, c->mu, c->stage, c->geo, c->ph, c->odd, c->stream));
+    LBM_CK(c, lbm::launch_fields(cur_state(c), c->phi, c->mu, c->stage, c->geo, c->ph,
+                                 read_pattern(c), c->stream));
   const size_t n = static_cast<size_t>(c->geo.n);
   const size_t s = c->geo.stride;
   std::vector<float> tmp;
@@ -305,8 +334,9 @@ lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
   if (!c) return LBM_EINVAL;
   if (!sum_phi || !mom) return fail(c, LBM_EINVAL, "outputs must not be NULL");
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
-  LBM_CK(c, lbm::launch_phi(c->pop, c->phi, c->geo, c->odd, c->stream));
-  LBM_CK(c, lbm::launch_reduce(c->pop, c->phi, c->partial, c->red, c->geo, c->odd, c->stream));
+  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, c->geo, read_pattern(c), c->stream));
+  LBM_CK(c, lbm::launch_reduce(cur_state(c), c->phi, c->partial, c->red, c->geo, read_pattern(c),
+                               c->stream));
   double h[5];
   LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
@@ -323,21 +353,19 @@ lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long
   if (!c) return LBM_EINVAL;
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
   const size_t n = static_cast<size_t>(c->geo.n);
-  for (int q = 0; q < lbm::kSlots; ++q) {
-    float* dst = q < 7 ? (f ? f + q * n : nullptr) : (g ? g + (q - 7) * n : nullptr);
+  for (int q = 0; q < lbm::kTileSlots; ++q) {
+    float* dst = nullptr;
+    if (q < 7)
+      dst = f ? f + q * n : nullptr;
+    else if (q < lbm::kSlots)
+      dst = g ? g + (q - 7) * n : nullptr;
+    else
+      dst = (phiu_prev && c->have_prev) ? phiu_prev + (q - lbm::kSlotPhiu) * n : nullptr;
     if (!dst) continue;
-    LBM_CK(c, lbm::launch_gather(c->pop, c->stage, c->geo, c->odd, q, c->stream));
+    LBM_CK(c, lbm::launch_gather(cur_state(c), c->stage, c->geo, read_pattern(c), q, c->stream));
     LBM_CK(c, cudaMemcpyAsync(dst, c->stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   }
-  if (phiu_prev) {
-    if (c->have_prev) {
-      for (int a = 0; a < 3; ++a)
-        LBM_CK(c, cudaMemcpyAsync(phiu_prev + a * n, c->phiu + a * c->geo.stride, n * sizeof(float),
-                                  cudaMemcpyDeviceToHost, c->stream));
-    } else {
-      std::memset(phiu_prev, 0, 3 * n * sizeof(float));
-    }
-  }
+  if (phiu_prev && !c->have_prev) std::memset(phiu_prev, 0, 3 * n * sizeof(float));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   if (step) *step = c->step;
   return LBM_OK;
@@ -349,19 +377,22 @@ lbm_status lbm_write_state(lbm_ctx* c, const float* f, const float* g, const flo
   if (!f || !g) return fail(c, LBM_EINVAL, "f and g must not be NULL");
   if (step < 0) return fail(c, LBM_EINVAL, "step must be >= 0");
   const size_t n = static_cast<size_t>(c->geo.n);
-  const size_t s = c->geo.stride;
-  // Even-step layout: pre-collision population q of cell x at slot (q, x).
-  for (int q = 0; q < lbm::kSlots; ++q) {
-    const float* src = q < 7 ? f + q * n : g + (q - 7) * n;
-    LBM_CK(c, cudaMemcpyAsync(c->pop + q * s, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  }
   const bool prev = phiu_prev && step > 0;
-  if (prev)
-    for (int a = 0; a < 3; ++a)
-      LBM_CK(c, cudaMemcpyAsync(c->phiu + a * s, phiu_prev + a * n, n * sizeof(float),
-                                cudaMemcpyHostToDevice, c->stream));
-  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->cur = 0;
   c->odd = false;
+  for (int q = 0; q < lbm::kTileSlots; ++q) {
+    const float* src = nullptr;
+    if (q < 7)
+      src = f + q * n;
+    else if (q < lbm::kSlots)
+      src = g + (q - 7) * n;
+    else if (prev)
+      src = phiu_prev + (q - lbm::kSlotPhiu) * n;
+    if (!src) continue;
+    LBM_CK(c, cudaMemcpyAsync(c->stage, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, lbm::launch_scatter(cur_state(c), c->stage, c->geo, read_pattern(c), q, c->stream));
+  }
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
   c->have_prev = prev;
   c->step = step;
   c->initialized = true;

@@ -13,13 +13,28 @@ namespace lbm {
 // ---------------------------------------------------------------------------------
 // Parameters passed by value to every kernel (kept in the constant bank).
 // ---------------------------------------------------------------------------------
+// Division of a non-negative int by a fixed divisor d >= 1 with one high multiply, an
+// add and a shift (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(m, n) + n) >> l for all 0 <= n < 2^31.
+struct FastDiv {
+  unsigned d, m, l;
+};
+
 struct Geometry {
   int nx, ny, nz;
   int walls;       // 1: halfway bounce-back at z = 0 and z = nz
   int n;           // cells, < 2^31
   int plane;       // nx * ny
-  size_t stride;   // elements between consecutive populations (= n)
+  size_t stride;   // elements between consecutive planes of dense per-cell arrays
+  FastDiv div_nx, div_ny;
 };
+
+__device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
+  const unsigned long long t =
+      static_cast<unsigned long long>(__umulhi(f.m, static_cast<unsigned>(n))) + static_cast<unsigned>(n);
+  return static_cast<int>(t >> f.l);
+}
 
 struct Physics {
   float rho_g;       // Eq. 14: rho = rho_g + (1 + phi) * half_drho
@@ -35,11 +50,30 @@ struct Physics {
 };
 
 // Population q of the D3Q7 set lives at slot q (0..6), population i of the D3Q15
-// set at slot 7 + i.  Velocity orders: Eq. 6 and Eq. 23.  In both orders the
-// opposite of i > 0 is i + 1 for odd i and i - 1 for even i.
+// set at slot 7 + i, and the three components of phi u of the previous step at slots
+// 22..24.  Velocity orders: Eq. 6 and Eq. 23.  In both orders the opposite of i > 0 is
+// i + 1 for odd i and i - 1 for even i.
 constexpr int kQ7 = 7;
 constexpr int kQ15 = 15;
-constexpr int kSlots = kQ7 + kQ15;
+constexpr int kSlots = kQ7 + kQ15;    // populations
+constexpr int kSlotPhiu = kSlots;     // first phi u slot
+constexpr int kTileSlots = kSlots + 3;
+
+// Cell-state layout: tiles of kTile consecutive cells (x fastest); a tile stores its
+// 25 slots one after another, kTile floats each (3.2 KB per tile).  A warp's own-cell
+// accesses therefore fall in one small block of memory instead of 25 arrays a whole
+// grid apart, which keeps the number of pages a warp touches small.
+constexpr int kTile = 32;
+constexpr int kTileShift = 5;
+
+__device__ __forceinline__ size_t tile_base(int i) {
+  return static_cast<size_t>(i >> kTileShift) * (kTileSlots * kTile) + (i & (kTile - 1));
+}
+
+template <int SLOT>
+__device__ __forceinline__ size_t slot_addr(int i) {
+  return tile_base(i) + SLOT * kTile;
+}
 
 // ---------------------------------------------------------------------------------
 // Neighbour offsets of one cell.  x and y wrap; z wraps or, between walls, the
@@ -76,39 +110,76 @@ __device__ __forceinline__ int offset(const Nbr& nb) {
 }
 
 // ---------------------------------------------------------------------------------
-// In-place "AA" population storage (one array, no second copy).
+// Population storage patterns.  A step reads the pre-collision populations of each
+// cell, collides, and stores the post-collision ones so that the next step finds its
+// pre-collision values.
 //
-// Even steps read population i of cell x from slot (i, x) and write the
-// post-collision value to slot (opp(i), x).  Odd steps read f_i(x) = f_i^+(x - c_i)
-// from slot (opp(i), x - c_i) and write the post-collision value to slot
-// (i, x + c_i), where the next even step finds it.  Each cell thus reads and writes
-// the same set of slots, so the update is race-free in place.  A link crossing a
-// wall is closed by bounce-back: in an odd step the read comes from slot (i, x) and
-// the write goes to slot (opp(i), x); even steps touch only their own cell.
+// kAB (two arrays, "pull"): the current array holds post-collision values of the
+//   previous step, slot (i, y) = f_i^+(y).  A step reads f_i(x) = f_i^+(x - c_i) from
+//   slot (i, x - c_i) of the current array and writes f_i^+(x) to slot (i, x) of the
+//   other array; the arrays then swap roles.  A link whose source x - c_i lies beyond
+//   a wall is closed by bounce-back: f_i(x) = f_opp(i)^+(x), slot (opp(i), x).
+// kAAEven / kAAOdd (one array, in place, half the memory): even steps read slot
+//   (i, x) and write to slot (opp(i), x); odd steps read f_i(x) from slot
+//   (opp(i), x - c_i) and write to slot (i, x + c_i), where the next even step finds
+//   it.  Each cell reads and writes the same set of slots, so the update is race-free
+//   in place.  Across a wall an odd step reads slot (i, x) and writes slot (opp(i), x).
+//   On GB300 the odd step, whose reads and writes both land on neighbours' lines in
+//   the array being updated, moves data markedly slower than the two-array pattern.
+//
+// The pointers carry no __restrict__: the in-place pattern loads and then stores the
+// same slots through one array, and those loads must stay ahead of the stores.
 // ---------------------------------------------------------------------------------
-// The pointers carry no __restrict__: the fused kernel loads and then stores the same
-// slots through one array, and those loads must stay ahead of the stores.
-template <bool ODD, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
-__device__ __forceinline__ float aa_load(const float* a, size_t stride, int idx,
-                                         const Nbr& nb) {
-  if (!ODD) return a[SLOT * stride + idx];
+enum Pattern { kAB = 0, kAAEven = 1, kAAOdd = 2 };
+
+template <int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+__device__ __forceinline__ float pop_load(const float* a, int idx, const Nbr& nb) {
+  if (P == kAAEven) return a[slot_addr<SLOT>(idx)];
   const bool wall = (CZ > 0 && nb.wlo) || (CZ < 0 && nb.whi);
-  if (wall) return a[SLOT * stride + idx];
-  return a[SLOT_OPP * stride + idx + offset<-CX, -CY, -CZ>(nb)];
+  if (P == kAAOdd) {
+    if (wall) return a[slot_addr<SLOT>(idx)];
+    return a[slot_addr<SLOT_OPP>(idx + offset<-CX, -CY, -CZ>(nb))];
+  }
+  if (wall) return a[slot_addr<SLOT_OPP>(idx)];
+  return a[slot_addr<SLOT>(idx + offset<-CX, -CY, -CZ>(nb))];
 }
 
-template <bool ODD, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
-__device__ __forceinline__ void aa_store(float* a, size_t stride, int idx,
-                                         const Nbr& nb, float v) {
-  if (!ODD) {
-    a[SLOT_OPP * stride + idx] = v;
+// Store the post-collision value of direction SLOT of cell idx.
+template <int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+__device__ __forceinline__ void pop_store(float* a, int idx, const Nbr& nb, float v) {
+  if (P == kAB) {
+    a[slot_addr<SLOT>(idx)] = v;
+  } else if (P == kAAEven) {
+    a[slot_addr<SLOT_OPP>(idx)] = v;
+  } else {
+    const bool wall = (CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo);
+    if (wall)
+      a[slot_addr<SLOT_OPP>(idx)] = v;
+    else
+      a[slot_addr<SLOT>(idx + offset<CX, CY, CZ>(nb))] = v;
+  }
+}
+
+// Place the PRE-collision value of direction SLOT of cell idx where a step of pattern
+// P reads it (inverse of pop_load): used to write initial and restored states.
+template <int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+__device__ __forceinline__ void pop_place(float* a, int idx, const Nbr& nb, float v) {
+  if (P == kAAEven) {
+    a[slot_addr<SLOT>(idx)] = v;
     return;
   }
-  const bool wall = (CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo);
+  const bool wall = (CZ > 0 && nb.wlo) || (CZ < 0 && nb.whi);
+  if (P == kAAOdd) {
+    if (wall)
+      a[slot_addr<SLOT>(idx)] = v;
+    else
+      a[slot_addr<SLOT_OPP>(idx + offset<-CX, -CY, -CZ>(nb))] = v;
+    return;
+  }
   if (wall)
-    a[SLOT_OPP * stride + idx] = v;
+    a[slot_addr<SLOT_OPP>(idx)] = v;
   else
-    a[SLOT * stride + idx + offset<CX, CY, CZ>(nb)] = v;
+    a[slot_addr<SLOT>(idx + offset<-CX, -CY, -CZ>(nb))] = v;
 }
 
 // D3Q7 velocities (Eq. 6) as template arguments: slot, opposite slot, c.
@@ -139,34 +210,44 @@ __device__ __forceinline__ void aa_store(float* a, size_t stride, int idx,
   X(13, 14, 1, -1, -1)    \
   X(14, 13, -1, 1, 1)
 
-template <bool ODD>
-__device__ __forceinline__ void load_f(const float* a, size_t s, int idx,
-                                       const Nbr& nb, float f[7]) {
-#define X(I, O, CX, CY, CZ) f[I] = aa_load<ODD, I, O, CX, CY, CZ>(a, s, idx, nb);
+template <int P>
+__device__ __forceinline__ void load_f(const float* a, int idx, const Nbr& nb, float f[7]) {
+#define X(I, O, CX, CY, CZ) f[I] = pop_load<P, I, O, CX, CY, CZ>(a, idx, nb);
   LBM_D3Q7_LIST(X)
 #undef X
 }
 
-template <bool ODD>
-__device__ __forceinline__ void store_f(float* a, size_t s, int idx, const Nbr& nb,
-                                        const float f[7]) {
-#define X(I, O, CX, CY, CZ) aa_store<ODD, I, O, CX, CY, CZ>(a, s, idx, nb, f[I]);
+template <int P>
+__device__ __forceinline__ void store_f(float* a, int idx, const Nbr& nb, const float f[7]) {
+#define X(I, O, CX, CY, CZ) pop_store<P, I, O, CX, CY, CZ>(a, idx, nb, f[I]);
   LBM_D3Q7_LIST(X)
 #undef X
 }
 
-template <bool ODD>
-__device__ __forceinline__ void load_g(const float* a, size_t s, int idx,
-                                       const Nbr& nb, float g[15]) {
-#define X(I, O, CX, CY, CZ) g[I] = aa_load<ODD, 7 + I, 7 + O, CX, CY, CZ>(a, s, idx, nb);
+template <int P>
+__device__ __forceinline__ void place_f(float* a, int idx, const Nbr& nb, const float f[7]) {
+#define X(I, O, CX, CY, CZ) pop_place<P, I, O, CX, CY, CZ>(a, idx, nb, f[I]);
+  LBM_D3Q7_LIST(X)
+#undef X
+}
+
+template <int P>
+__device__ __forceinline__ void load_g(const float* a, int idx, const Nbr& nb, float g[15]) {
+#define X(I, O, CX, CY, CZ) g[I] = pop_load<P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb);
   LBM_D3Q15_LIST(X)
 #undef X
 }
 
-template <bool ODD>
-__device__ __forceinline__ void store_g(float* a, size_t s, int idx, const Nbr& nb,
-                                        const float g[15]) {
-#define X(I, O, CX, CY, CZ) aa_store<ODD, 7 + I, 7 + O, CX, CY, CZ>(a, s, idx, nb, g[I]);
+template <int P>
+__device__ __forceinline__ void store_g(float* a, int idx, const Nbr& nb, const float g[15]) {
+#define X(I, O, CX, CY, CZ) pop_store<P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb, g[I]);
+  LBM_D3Q15_LIST(X)
+#undef X
+}
+
+template <int P>
+__device__ __forceinline__ void place_g(float* a, int idx, const Nbr& nb, const float g[15]) {
+#define X(I, O, CX, CY, CZ) pop_place<P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb, g[I]);
   LBM_D3Q15_LIST(X)
 #undef X
 }

@@ -10,18 +10,30 @@ namespace lbm {
 // Upper bound on the number of per-block partial sums of the FP64 reduction.
 constexpr int kReduceMaxParts = 1024;
 
-cudaError_t launch_phi(const float* pop, float* phi, const Geometry& geo, bool odd,
+cudaError_t launch_phi(const float* src, float* phi, const Geometry& geo, int pattern,
                        cudaStream_t st);
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st);
-cudaError_t launch_collide(float* pop, float* phiu, const float* phi, const float* mu,
-                           const Geometry& geo, const Physics& ph, bool odd, bool have_prev,
+cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
+                           const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                            cudaStream_t st);
-cudaError_t launch_fields(const float* pop, const float* phi, const float* mu, float* out,
-                          const Geometry& geo, const Physics& ph, bool odd, cudaStream_t st);
-cudaError_t launch_init(float* pop, float* phiu, const float* phi, const float* mu,
-                        const float* u0, const float* p0, const Geometry& geo,
-                        const Physics& ph, cudaStream_t st);
+cudaError_t launch_fields(const float* src, const float* phi, const float* mu, float* out,
+                          const Geometry& geo, const Physics& ph, int pattern, cudaStream_t st);
+cudaError_t launch_init(float* state, const float* phi, const float* mu, const float* u0,
+                        const float* p0, const Geometry& geo, const Physics& ph, int pattern,
+                        cudaStream_t st);
+cudaError_t launch_gather(const float* src, float* dense, const Geometry& geo, int pattern,
+                          int slot, cudaStream_t st);
+cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
+                           int slot, cudaStream_t st);
+cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
+int reduce_parts(const Geometry& geo);
+cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
+                          const Geometry& geo, int pattern, cudaStream_t st);
+// Floats of the tiled cell-state array for n cells.
+inline size_t state_floats(int n) {
+  return static_cast<size_t>((n + kTile - 1) / kTile) * kTileSlots * kTile;
+}
 cudaError_t launch_gather(const float* pop, float* dense, const Geometry& geo, bool odd,
                           int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);

@@ -6,8 +6,9 @@
 //   k_phi      phi = sum_i f_i of the streamed populations (Eqs. 13, 16)
 //   k_mu       mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2, Eq. 36)
 //   k_collide  fused: pull f and g, stencils of phi and mu, forces, u and p, both MRT
-//              collisions, d_t(phi u), push f+ and g+ (Eqs. 14-34)
+//              collisions, d_t(phi u), store f+ and g+ (Eqs. 14-34)
 // plus initialisation, field read-out, state gather/scatter and the FP64 reduction.
+// Every kernel is templated on the population storage pattern (lbm_device.cuh).
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -20,15 +21,15 @@ namespace {
 constexpr int kBlock = 256;
 
 __device__ __forceinline__ void cell_coords(const Geometry& geo, int idx, int& x, int& y, int& z) {
-  x = idx % geo.nx;
-  const int r = idx / geo.nx;
-  y = r % geo.ny;
-  z = r / geo.ny;
+  const int r = fast_div(idx, geo.div_nx);
+  x = idx - r * geo.nx;
+  z = fast_div(r, geo.div_ny);
+  y = r - z * geo.ny;
 }
 
 // ------------------------------------------------------------------ k_phi ---------
-template <bool ODD>
-__global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ pop,
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
                                                 float* __restrict__ phi, Geometry geo) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
@@ -36,78 +37,130 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ pop,
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
   float f[7];
-  load_f<ODD>(pop, geo.stride, idx, nb, f);
+  load_f<P>(src, idx, nb, f);
   phi[idx] = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]));
 }
 
 // ------------------------------------------------------------------- k_mu ---------
-__global__ void __launch_bounds__(kBlock) k_mu(const float* __restrict__ phi,
-                                               float* __restrict__ mu, Geometry geo,
-                                               Physics ph) {
-  const int idx = blockIdx.x * kBlock + threadIdx.x;
-  if (idx >= geo.n) return;
-  int x, y, z;
-  cell_coords(geo, idx, x, y, z);
-  const Nbr nb = make_nbr(geo, x, y, z);
-  Stencil s;
-  load_stencil(phi, idx, nb, s);
-  mu[idx] = chemical_potential(ph, s.c, stencil_lap(s));
+// Shared-memory tiling of the 15-point stencil: a block computes a kTX x kTY x kTZ
+// brick of cells from one load of the brick plus a one-cell halo, so each phi value is
+// read from global memory about (kTX+2)(kTY+2)(kTZ+2)/(kTX kTY kTZ) = 1.7 times
+// instead of 15 times, and all of a thread's loads are in flight together.
+constexpr int kTX = 32, kTY = 8, kTZ = 8;
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;
+
+// v mod n for v in [-1, n + span): a compare and add when n >= span, else a modulo.
+__device__ __forceinline__ int wrap(int v, int n, int span) {
+  if (n >= span) return v < 0 ? v + n : (v >= n ? v - n : v);
+  v %= n;
+  return v < 0 ? v + n : v;
 }
 
-// -------------------------------------------------------------- k_collide ---------
-template <bool ODD>
-__global__ void __launch_bounds__(kBlock) k_collide(float* pop,
-                                                    float* __restrict__ phiu,
-                                                    const float* __restrict__ phi,
-                                                    const float* __restrict__ mu,
-                                                    Geometry geo, Physics ph, int have_prev) {
-  const int idx = blockIdx.x * kBlock + threadIdx.x;
-  if (idx >= geo.n) return;
-  int x, y, z;
-  cell_coords(geo, idx, x, y, z);
-  const Nbr nb = make_nbr(geo, x, y, z);
+__global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
+                                                 float* __restrict__ mu, Geometry geo,
+                                                 Physics ph) {
+  __shared__ float tile[kHZ][kHY][kHX];
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  // brick + halo; x, y wrap; z wraps or, between walls, clamps (ghost = adjacent node)
+  for (int k = tid; k < kHX * kHY * kHZ; k += kTX * kTY) {
+    const int j = k % kHX, i = (k / kHX) % kHY, l = k / (kHX * kHY);
+    const int gx = wrap(x0 - 1 + j, geo.nx, kHX), gy = wrap(y0 - 1 + i, geo.ny, kHY);
+    const int zz = z0 - 1 + l;
+    const int gz = geo.walls ? min(max(zz, 0), geo.nz - 1) : wrap(zz, geo.nz, kHZ);
+    tile[l][i][j] = __ldg(phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx + gx);
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const int i = threadIdx.y + 1, j = threadIdx.x + 1;
+  for (int l = 1; l <= kTZ && z0 + l - 1 < geo.nz; ++l) {
+    Stencil s;
+    s.c = tile[l][i][j];
+    s.xm = tile[l][i][j - 1];
+    s.xp = tile[l][i][j + 1];
+    s.ym = tile[l][i - 1][j];
+    s.yp = tile[l][i + 1][j];
+    s.zm = tile[l - 1][i][j];
+    s.zp = tile[l + 1][i][j];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      s.k[b] = tile[(b & 4) ? l + 1 : l - 1][(b & 2) ? i + 1 : i - 1][(b & 1) ? j + 1 : j - 1];
+    const int z = z0 + l - 1;
+    mu[(static_cast<size_t>(z) * geo.ny + y) * geo.nx + x] = chemical_potential(ph, s.c, stencil_lap(s));
+  }
+}
 
-  float grad_phi[3], lap_mu, phi_c, mu_c;
+// Stencil quantities of one cell: grad phi (Eq. 35), lap mu (Eq. 36), centre values.
+struct CellStencils {
+  float grad_phi[3], lap_mu, phi, mu;
+};
+
+__device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ phi,
+                                                      const float* __restrict__ mu, int idx,
+                                                      const Nbr& nb) {
+  CellStencils cs;
   {
     Stencil s;
     load_stencil(phi, idx, nb, s);
-    stencil_grad(s, grad_phi);
-    phi_c = s.c;
+    stencil_grad(s, cs.grad_phi);
+    cs.phi = s.c;
   }
   {
     Stencil s;
     load_stencil(mu, idx, nb, s);
-    lap_mu = stencil_lap(s);
-    mu_c = s.c;
+    cs.lap_mu = stencil_lap(s);
+    cs.mu = s.c;
   }
+  return cs;
+}
 
-  float g[15];
-  load_g<ODD>(pop, geo.stride, idx, nb, g);
-  const Macro M = macroscopic(ph, g, phi_c, mu_c, grad_phi, lap_mu);
-  const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + phi_c * ph.half_dnu) + 0.5f);
+// -------------------------------------------------------------- k_collide ---------
+// src and dst are the same array for the in-place patterns.  All 25 cell-state loads
+// are issued first so that they are in flight together with the stencil loads.
+#ifndef LBM_COLLIDE_MIN_BLOCKS
+#define LBM_COLLIDE_MIN_BLOCKS 3
+#endif
+template <int P>
+__global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
+    k_collide(const float* src, float* dst, const float* __restrict__ phi,
+              const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev) {
+  const int idx = blockIdx.x * kBlock + threadIdx.x;
+  if (idx >= geo.n) return;
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
+
+  float g[15], f[7], prev[3];
+  load_g<P>(src, idx, nb, g);
+  load_f<P>(src, idx, nb, f);
+  const size_t own = tile_base(idx) + kSlotPhiu * kTile;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) prev[a] = src[own + a * kTile];
+
+  const CellStencils cs = cell_stencils(phi, mu, idx, nb);
+  const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
+  const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
   collide_d3q15(ph, g, M, lambda_visc);
-  store_g<ODD>(pop, geo.stride, idx, nb, g);
+  store_g<P>(dst, idx, nb, g);
 
-  // d_t(phi u) by the backward difference of Eq. 34
+  // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
   float dphiu[3];
-  const size_t s = geo.stride;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float cur = phi_c * M.u[a];
-    dphiu[a] = have_prev ? cur - phiu[a * s + idx] : 0.0f;
-    phiu[a * s + idx] = cur;
+    const float cur = cs.phi * M.u[a];
+    dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
+    dst[own + a * kTile] = cur;
   }
 
-  float f[7];
-  load_f<ODD>(pop, geo.stride, idx, nb, f);
-  collide_d3q7(ph, f, phi_c, mu_c, M.u, dphiu);
-  store_f<ODD>(pop, geo.stride, idx, nb, f);
+  collide_d3q7(ph, f, cs.phi, cs.mu, M.u, dphiu);
+  store_f<P>(dst, idx, nb, f);
 }
 
 // --------------------------------------------------------------- k_fields ---------
 // rho, p, u of the current populations into out[0..4] (rho, p, ux, uy, uz).
-template <bool ODD>
-__global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ pop,
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src,
                                                    const float* __restrict__ phi,
                                                    const float* __restrict__ mu,
                                                    float* __restrict__ out, Geometry geo,
@@ -117,22 +170,10 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ pop
   int x, y, z;
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
-  float grad_phi[3], lap_mu, phi_c, mu_c;
-  {
-    Stencil s;
-    load_stencil(phi, idx, nb, s);
-    stencil_grad(s, grad_phi);
-    phi_c = s.c;
-  }
-  {
-    Stencil s;
-    load_stencil(mu, idx, nb, s);
-    lap_mu = stencil_lap(s);
-    mu_c = s.c;
-  }
+  const CellStencils cs = cell_stencils(phi, mu, idx, nb);
   float g[15];
-  load_g<ODD>(pop, geo.stride, idx, nb, g);
-  const Macro M = macroscopic(ph, g, phi_c, mu_c, grad_phi, lap_mu);
+  load_g<P>(src, idx, nb, g);
+  const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   const size_t s = geo.stride;
   out[0 * s + idx] = M.rho;
   out[1 * s + idx] = M.p;
@@ -142,17 +183,19 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ pop
 }
 
 // ------------------------------------------------------------------ k_init --------
-// f = f^eq (Eq. 5), g = g^eq (Eq. 21) in the even-step layout; phi u stored.
-// u0 and p0 may be null (zero).
-__global__ void __launch_bounds__(kBlock) k_init(float* __restrict__ pop,
-                                                 float* __restrict__ phiu,
-                                                 const float* __restrict__ phi,
+// Pre-collision populations f = f^eq (Eq. 5), g = g^eq (Eq. 21) placed for a step of
+// pattern P; phi u stored in the own tile.  u0 (3 dense planes) and p0 may be null.
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __restrict__ phi,
                                                  const float* __restrict__ mu,
                                                  const float* __restrict__ u0,
                                                  const float* __restrict__ p0, Geometry geo,
                                                  Physics ph) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
   const size_t s = geo.stride;
   const float ph_ = phi[idx], mu_ = mu[idx];
   float u[3] = {0.0f, 0.0f, 0.0f};
@@ -167,37 +210,35 @@ __global__ void __launch_bounds__(kBlock) k_init(float* __restrict__ pop,
   // D3Q7: omega_0 = 1 - 3A, omega_i = A/2, c_s^2 = A
   const float emu = ph.eta * mu_;
   const float hw = 0.5f * ph.A * emu;
-  pop[0 * s + idx] = ph_ - 3.0f * ph.A * emu;
   const float jx = 0.5f * ph_ * u[0], jy = 0.5f * ph_ * u[1], jz = 0.5f * ph_ * u[2];
-  pop[1 * s + idx] = hw + jx;
-  pop[2 * s + idx] = hw - jx;
-  pop[3 * s + idx] = hw + jy;
-  pop[4 * s + idx] = hw - jy;
-  pop[5 * s + idx] = hw + jz;
-  pop[6 * s + idx] = hw - jz;
+  const float f[7] = {ph_ - 3.0f * ph.A * emu, hw + jx, hw - jx, hw + jy, hw - jy, hw + jz, hw - jz};
+  place_f<P>(state, idx, nb, f);
 
   // D3Q15: g_i = 3 p omega_i + rho omega_i (3 c.u + 9/2 (c.u)^2 - 3/2 u^2), g_0 -= 3p
   const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   constexpr int cx[15] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
   constexpr int cy[15] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, -1, 1, -1, 1};
   constexpr int cz[15] = {0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1, -1, 1};
+  float g[15];
 #pragma unroll
   for (int i = 0; i < 15; ++i) {
     const float w = i == 0 ? 2.0f / 9.0f : (i < 7 ? 1.0f / 9.0f : 1.0f / 72.0f);
     const float cu = cx[i] * u[0] + cy[i] * u[1] + cz[i] * u[2];
-    float v = 3.0f * p * w + rho * w * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-    if (i == 0) v -= 3.0f * p;
-    pop[(7 + i) * s + idx] = v;
+    g[i] = 3.0f * p * w + rho * w * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
   }
-  phiu[0 * s + idx] = ph_ * u[0];
-  phiu[1 * s + idx] = ph_ * u[1];
-  phiu[2 * s + idx] = ph_ * u[2];
+  g[0] -= 3.0f * p;
+  place_g<P>(state, idx, nb, g);
+  const size_t own = tile_base(idx) + kSlotPhiu * kTile;
+  state[own + 0 * kTile] = ph_ * u[0];
+  state[own + 1 * kTile] = ph_ * u[1];
+  state[own + 2 * kTile] = ph_ * u[2];
 }
 
 // -------------------------------------------------- state gather / scatter --------
-// Population `slot` of the current (pre-collision) state to dense[idx].
-template <bool ODD>
-__global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ pop,
+// Slot `slot` of the current pre-collision state to dense[idx]: populations through
+// the pattern's addressing, phi u (slots 22..24) from the own tile.
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ src,
                                                    float* __restrict__ dense, Geometry geo,
                                                    int slot) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
@@ -206,20 +247,52 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ pop
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
   float v = 0.0f;
-  if (slot < 7) {
-    float f[7];
-    load_f<ODD>(pop, geo.stride, idx, nb, f);
-#pragma unroll
-    for (int q = 0; q < 7; ++q)
-      if (q == slot) v = f[q];
-  } else {
-    float g[15];
-    load_g<ODD>(pop, geo.stride, idx, nb, g);
-#pragma unroll
-    for (int q = 0; q < 15; ++q)
-      if (q == slot - 7) v = g[q];
+  switch (slot) {
+#define X(I, O, CX, CY, CZ) \
+  case I:                   \
+    v = pop_load<P, I, O, CX, CY, CZ>(src, idx, nb); \
+    break;
+    LBM_D3Q7_LIST(X)
+#undef X
+#define X(I, O, CX, CY, CZ) \
+  case 7 + I:               \
+    v = pop_load<P, 7 + I, 7 + O, CX, CY, CZ>(src, idx, nb); \
+    break;
+    LBM_D3Q15_LIST(X)
+#undef X
+    default:
+      v = src[tile_base(idx) + slot * kTile];
   }
   dense[idx] = v;
+}
+
+// dense[idx] = pre-collision value of slot `slot` of cell idx, placed where a step of
+// pattern P reads it (the inverse of k_gather).
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_scatter(float* state, const float* __restrict__ dense,
+                                                    Geometry geo, int slot) {
+  const int idx = blockIdx.x * kBlock + threadIdx.x;
+  if (idx >= geo.n) return;
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
+  const float v = dense[idx];
+  switch (slot) {
+#define X(I, O, CX, CY, CZ) \
+  case I:                   \
+    pop_place<P, I, O, CX, CY, CZ>(state, idx, nb, v); \
+    break;
+    LBM_D3Q7_LIST(X)
+#undef X
+#define X(I, O, CX, CY, CZ) \
+  case 7 + I:               \
+    pop_place<P, 7 + I, 7 + O, CX, CY, CZ>(state, idx, nb, v); \
+    break;
+    LBM_D3Q15_LIST(X)
+#undef X
+    default:
+      state[tile_base(idx) + slot * kTile] = v;
+  }
 }
 
 __global__ void __launch_bounds__(kBlock) k_convert(const double* __restrict__ in,
@@ -229,10 +302,11 @@ __global__ void __launch_bounds__(kBlock) k_convert(const double* __restrict__ i
 }
 
 // --------------------------------------------------------------- k_reduce ---------
-// Pass 1: block b sums cells b, b + B, ... in FP64 (fixed order: grid-stride by block
-// rows, then a fixed shuffle tree).  partial[b] = {sum phi, jx, jy, jz, non-finite}.
-template <bool ODD>
-__global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restrict__ pop,
+// Pass 1: block b sums cells b*256 + t, then strides by the grid, in FP64 (fixed
+// order: grid-stride rows, then a fixed shuffle tree).
+// partial[b] = {sum phi, jx, jy, jz, non-finite count}.
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restrict__ src,
                                                            const float* __restrict__ phi,
                                                            double* __restrict__ partial,
                                                            Geometry geo) {
@@ -242,7 +316,7 @@ __global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restri
     cell_coords(geo, idx, x, y, z);
     const Nbr nb = make_nbr(geo, x, y, z);
     float g[15];
-    load_g<ODD>(pop, geo.stride, idx, nb, g);
+    load_g<P>(src, idx, nb, g);
     const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12], d13 = g[13] - g[14];
     const float jx = (g[1] - g[2]) + ((d7 + d9) + (d11 + d13));
     const float jy = (g[3] - g[4]) + ((d7 + d9) - (d11 + d13));
@@ -290,56 +364,62 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double* __restric
 
 inline unsigned blocks_for(int n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
+// Host-side dispatch of a kernel template over the three patterns.
+#define LBM_DISPATCH(pattern, KERNEL, ...)                                          \
+  do {                                                                            \
+    if ((pattern) == kAB)                                                         \
+      KERNEL<kAB><<<blocks_for(geo.n), kBlock, 0, st>>>(__VA_ARGS__);             \
+    else if ((pattern) == kAAEven)                                                \
+      KERNEL<kAAEven><<<blocks_for(geo.n), kBlock, 0, st>>>(__VA_ARGS__);         \
+    else                                                                          \
+      KERNEL<kAAOdd><<<blocks_for(geo.n), kBlock, 0, st>>>(__VA_ARGS__);          \
+  } while (0)
+
 }  // namespace
 
 // ------------------------------------------------------------ host launchers ------
-cudaError_t launch_phi(const float* pop, float* phi, const Geometry& geo, bool odd,
+cudaError_t launch_phi(const float* src, float* phi, const Geometry& geo, int pattern,
                        cudaStream_t st) {
-  if (odd)
-    k_phi<true><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phi, geo);
-  else
-    k_phi<false><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phi, geo);
+  LBM_DISPATCH(pattern, k_phi, src, phi, geo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st) {
-  k_mu<<<blocks_for(geo.n), kBlock, 0, st>>>(phi, mu, geo, ph);
+  const dim3 grid((geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY, (geo.nz + kTZ - 1) / kTZ);
+  k_mu<<<grid, dim3(kTX, kTY), 0, st>>>(phi, mu, geo, ph);
   return cudaGetLastError();
 }
 
-cudaError_t launch_collide(float* pop, float* phiu, const float* phi, const float* mu,
-                           const Geometry& geo, const Physics& ph, bool odd, bool have_prev,
+cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
+                           const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                            cudaStream_t st) {
-  if (odd)
-    k_collide<true><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phiu, phi, mu, geo, ph, have_prev);
-  else
-    k_collide<false><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phiu, phi, mu, geo, ph, have_prev);
+  LBM_DISPATCH(pattern, k_collide, src, dst, phi, mu, geo, ph, have_prev ? 1 : 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fields(const float* pop, const float* phi, const float* mu, float* out,
-                          const Geometry& geo, const Physics& ph, bool odd, cudaStream_t st) {
-  if (odd)
-    k_fields<true><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phi, mu, out, geo, ph);
-  else
-    k_fields<false><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phi, mu, out, geo, ph);
+cudaError_t launch_fields(const float* src, const float* phi, const float* mu, float* out,
+                          const Geometry& geo, const Physics& ph, int pattern, cudaStream_t st) {
+  LBM_DISPATCH(pattern, k_fields, src, phi, mu, out, geo, ph);
   return cudaGetLastError();
 }
 
-cudaError_t launch_init(float* pop, float* phiu, const float* phi, const float* mu,
-                        const float* u0, const float* p0, const Geometry& geo,
-                        const Physics& ph, cudaStream_t st) {
-  k_init<<<blocks_for(geo.n), kBlock, 0, st>>>(pop, phiu, phi, mu, u0, p0, geo, ph);
+cudaError_t launch_init(float* state, const float* phi, const float* mu, const float* u0,
+                        const float* p0, const Geometry& geo, const Physics& ph, int pattern,
+                        cudaStream_t st) {
+  LBM_DISPATCH(pattern, k_init, state, phi, mu, u0, p0, geo, ph);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const float* pop, float* dense, const Geometry& geo, bool odd,
+cudaError_t launch_gather(const float* src, float* dense, const Geometry& geo, int pattern,
                           int slot, cudaStream_t st) {
-  if (odd)
-    k_gather<true><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, dense, geo, slot);
-  else
-    k_gather<false><<<blocks_for(geo.n), kBlock, 0, st>>>(pop, dense, geo, slot);
+  LBM_DISPATCH(pattern, k_gather, src, dense, geo, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
+                           int slot, cudaStream_t st) {
+  LBM_DISPATCH(pattern, k_scatter, state, dense, geo, slot);
   return cudaGetLastError();
 }
 
@@ -353,13 +433,15 @@ int reduce_parts(const Geometry& geo) {
   return b < kReduceMaxParts ? b : kReduceMaxParts;
 }
 
-cudaError_t launch_reduce(const float* pop, const float* phi, double* partial, double* out,
-                          const Geometry& geo, bool odd, cudaStream_t st) {
+cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
+                          const Geometry& geo, int pattern, cudaStream_t st) {
   const int parts = reduce_parts(geo);
-  if (odd)
-    k_reduce_partial<true><<<parts, kBlock, 0, st>>>(pop, phi, partial, geo);
+  if (pattern == kAB)
+    k_reduce_partial<kAB><<<parts, kBlock, 0, st>>>(src, phi, partial, geo);
+  else if (pattern == kAAEven)
+    k_reduce_partial<kAAEven><<<parts, kBlock, 0, st>>>(src, phi, partial, geo);
   else
-    k_reduce_partial<false><<<parts, kBlock, 0, st>>>(pop, phi, partial, geo);
+    k_reduce_partial<kAAOdd><<<parts, kBlock, 0, st>>>(src, phi, partial, geo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_final<<<1, kBlock, 0, st>>>(partial, parts, out);

@@ -26,6 +26,8 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
 
 LBM_FLAG_BUOYANCY = 1
 LBM_STORAGE_FP32 = 0
+LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
+PATTERNS = {"ab": LBM_PATTERN_AB, "aa": LBM_PATTERN_AA}
 
 LBM_FIELD_PHI, LBM_FIELD_RHO, LBM_FIELD_P, LBM_FIELD_U, LBM_FIELD_MU = 1, 2, 4, 8, 16
 LBM_FIELD_ALL = 31
@@ -48,7 +50,8 @@ class LbmParams(Structure):
     _fields_ = [("rho_l", c_double), ("rho_g", c_double), ("nu_l", c_double), ("nu_g", c_double),
                 ("mobility", c_double), ("D", c_double), ("sigma", c_double),
                 ("g", c_double * 3), ("A", c_double), ("sf", c_double * 7),
-                ("sg", c_double * 15), ("flags", c_uint), ("storage", c_int)]
+                ("sg", c_double * 15), ("flags", c_uint), ("storage", c_int),
+                ("pattern", c_int)]
 
 
 ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p)
@@ -112,7 +115,7 @@ def _ptr(a: Optional[np.ndarray]):
 
 def make_params(rho_l, rho_g, nu_l, nu_g, mobility, D, sigma, g=(0.0, 0.0, 0.0), A=0.25,
                 sf=(1.0, 1.25, 1.25, 1.25, 1.2, 1.0, 1.0), sg=(1.0,) * 15, buoyancy=False,
-                storage=LBM_STORAGE_FP32) -> LbmParams:
+                storage=LBM_STORAGE_FP32, pattern=LBM_PATTERN_AB) -> LbmParams:
     p = LbmParams()
     p.rho_l, p.rho_g, p.nu_l, p.nu_g = rho_l, rho_g, nu_l, nu_g
     p.mobility, p.D, p.sigma, p.A = mobility, D, sigma, A
@@ -121,13 +124,14 @@ def make_params(rho_l, rho_g, nu_l, nu_g, mobility, D, sigma, g=(0.0, 0.0, 0.0),
     p.sg[:] = [float(v) for v in sg]
     p.flags = LBM_FLAG_BUOYANCY if buoyancy else 0
     p.storage = storage
+    p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
     return p
 
 
-def params_from_workload(w) -> tuple:
+def params_from_workload(w, pattern=LBM_PATTERN_AB) -> tuple:
     grid = LbmGrid(w.nx, w.ny, w.nz, 1 if w.walls_z else 0)
     params = make_params(w.rho_l, w.rho_g, w.nu_l, w.nu_g, w.mobility, w.D, w.sigma, w.g, w.A,
-                         w.sf, w.sg, w.buoyancy)
+                         w.sf, w.sg, w.buoyancy, pattern=pattern)
     return grid, params
 
 
@@ -304,9 +308,9 @@ class Solver:
     """One simulation: create from a workload, initialise, step, read."""
 
     def __init__(self, workload, stream: Optional[int] = None, allocator: str = "torch",
-                 init: bool = True):
+                 init: bool = True, pattern=LBM_PATTERN_AB):
         self.workload = workload
-        grid, params = params_from_workload(workload)
+        grid, params = params_from_workload(workload, pattern)
         self.ctx = lbm_create(grid, params, stream=stream, allocator=allocator)
         if init:
             lbm_init_phi(self.ctx, workload.phi0, workload.u0, workload.p0)

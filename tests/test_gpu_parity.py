@@ -52,11 +52,12 @@ def test_initial_fields(L):
     np.testing.assert_allclose(gf["mu"], of["mu"], atol=1e-7)
 
 
-def test_droplet_100_steps(L):
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_droplet_100_steps(L, pattern):
     """The static droplet (32^3, R = 8, D = 4, sigma = 0.01, rho 3:1, nu = 0.1,
     Mob = 0.1), seeded velocity and pressure noise so every term acts."""
     w = I.perturbed(I.droplet(n=32, R=8.0), seed=0, u_amp=0.005, p_amp=1e-4)
-    with L.Solver(w) as s:
+    with L.Solver(w, pattern=pattern) as s:
         s.step(100)
         gf = s.fields()
         assert s.t == 100
@@ -65,14 +66,15 @@ def test_droplet_100_steps(L):
     _compare_fields(gf, o.fields(), w.U, p_tol=1e-6)
 
 
-def test_rayleigh_taylor_ragged_100_steps(L):
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_rayleigh_taylor_ragged_100_steps(L, pattern):
     """Walls in z, gravity, ragged sizes in all three directions (not multiples of a
     block or a warp)."""
     w = I.rayleigh_taylor(W=37, nz=70, Re=256.0)
     w.ny = 29
     w.phi0 = np.ascontiguousarray(w.phi0[:, :29, :])
     w = I.perturbed(w, seed=2, u_amp=0.01, p_amp=1e-4)
-    with L.Solver(w) as s:
+    with L.Solver(w, pattern=pattern) as s:
         s.step(100)
         gf = s.fields()
     o = _oracle(w)
@@ -99,16 +101,17 @@ def test_every_term_and_option(L):
     _compare_fields(gf, o.fields(), 0.01, p_tol=1e-6)
 
 
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("shape,walls", [((1, 1, 1), False), ((1, 5, 7), False), ((3, 1, 4), True),
                                          ((1, 2, 3), True), ((5, 3, 2), False), ((9, 33, 1), True)])
-def test_degenerate_grids(L, shape, walls):
+def test_degenerate_grids(L, shape, walls, pattern):
     """Grids one cell thick in some direction, a single cell, walls one cell apart."""
     nz, ny, nx = shape
     w = I.droplet(n=4, R=1.5, nx=nx, ny=ny, nz=nz)
     w.walls_z = walls
     w = I.perturbed(w, seed=4, phi_amp=0.3, u_amp=0.01, p_amp=1e-3)
     w.g = (1e-5, 0.0, -2e-5)
-    with L.Solver(w) as s:
+    with L.Solver(w, pattern=pattern) as s:
         s.step(20)
         gf = s.fields()
     o = _oracle(w)
@@ -116,8 +119,9 @@ def test_degenerate_grids(L, shape, walls):
     _compare_fields(gf, o.fields(), 0.01)
 
 
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("walls", [False, True])
-def test_state_after_one_and_two_steps(L, walls):
+def test_state_after_one_and_two_steps(L, walls, pattern):
     """Raw populations against the oracle after one (odd layout) and two (even layout)
     steps: within a few FP32 ulps of the population magnitudes."""
     if walls:
@@ -125,7 +129,7 @@ def test_state_after_one_and_two_steps(L, walls):
     else:
         w = I.perturbed(I.droplet(n=12, R=4.0, nx=13, ny=12, nz=11), seed=5, u_amp=0.02, p_amp=1e-3)
     o = _oracle(w)
-    with L.Solver(w) as s:
+    with L.Solver(w, pattern=pattern) as s:
         for k in (1, 2):
             s.step(1)
             o.step(1)
@@ -136,11 +140,11 @@ def test_state_after_one_and_two_steps(L, walls):
             np.testing.assert_allclose(phiu, o.phiu_prev, atol=1e-7)
 
 
-def _sampled_one_step(L, w, warm_steps, n_samples, seed):
+def _sampled_one_step(L, w, warm_steps, n_samples, seed, pattern="ab"):
     """Run warm_steps on the GPU, take its state, advance one more step on the GPU and,
     at sampled cells, with the oracle from the same state."""
     p = O.Params.from_workload(w)
-    with L.Solver(w) as s:
+    with L.Solver(w, pattern=pattern) as s:
         s.step(warm_steps)
         f, g, phiu, _ = s.state()
         s.step(1)
@@ -154,11 +158,12 @@ def _sampled_one_step(L, w, warm_steps, n_samples, seed):
     np.testing.assert_allclose(gg, og, atol=2e-6 * np.abs(og).max() + 1e-9)
 
 
-def test_full_size_rayleigh_taylor_64(L):
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_full_size_rayleigh_taylor_64(L, pattern):
     """Coupled Rayleigh-Taylor at its full size (64 x 64 x 256, Re = 256, At = 0.5):
     one step at 200 sampled cells (plus the box corners) after 99 GPU steps."""
     w = I.rayleigh_taylor(W=64, Re=256.0)
-    _sampled_one_step(L, w, 99, 200, seed=7)
+    _sampled_one_step(L, w, 99, 200, seed=7, pattern=pattern)
 
 
 def test_full_size_rayleigh_taylor_256(L):
@@ -190,17 +195,20 @@ def test_reduce_matches_oracle(L):
     np.testing.assert_allclose(mom, omom, atol=1e-6 * w.cells * 1e-2)
 
 
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("k", [3, 4])
-def test_resume_is_bit_exact(L, k):
-    """Read the state after k steps (odd and even layouts), continue 5 steps; a fresh
-    context resumed from that state gives the same populations bit for bit."""
+def test_resume_is_bit_exact(L, k, pattern):
+    """Read the state after k steps (odd and even step counts), continue 5 steps; a
+    fresh context resumed from that state gives the same populations bit for bit, also
+    when it resumes with the other storage pattern."""
     w = I.perturbed(I.rayleigh_taylor(W=16, nz=24, Re=100.0), seed=11, u_amp=0.01, p_amp=1e-3)
-    with L.Solver(w) as a:
+    with L.Solver(w, pattern=pattern) as a:
         a.step(k)
         st = a.state()
         a.step(5)
         ref = a.state()
-    with L.Solver(w, init=False) as b:
+    other = "aa" if pattern == "ab" else "ab"
+    with L.Solver(w, init=False, pattern=other) as b:
         b.set_state(st[0], st[1], st[2], st[3])
         assert b.t == k
         b.step(5)
@@ -248,3 +256,17 @@ def test_profile_counts_launches(L):
             ms, n = L.lbm_profile_read(s.ctx, k)
             assert n == 6 and ms > 0
         L.lbm_profile(s.ctx, False)
+
+
+def test_patterns_agree_bit_for_bit(L):
+    """The two-array and the in-place storage patterns run the same arithmetic: after
+    any number of steps their states are identical."""
+    w = I.perturbed(I.rayleigh_taylor(W=20, nz=36, Re=200.0), seed=12, phi_amp=0.02,
+                    u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w, pattern="ab") as a, L.Solver(w, pattern="aa") as b:
+        for n in (1, 2, 5):
+            a.step(n)
+            b.step(n)
+            sa, sb = a.state(), b.state()
+            for x, y in zip(sa[:3], sb[:3]):
+                assert np.array_equal(x, y)
