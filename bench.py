@@ -48,7 +48,10 @@ STEP_BYTES_PER_CELL = COLLIDE_BYTES_PER_CELL + (7 + 1) * 4 + (1 + 1) * 4  # + k_
 # DRAM traffic of k_collide per cell from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the cells of the captured launch), valid only for
 # the kernel source it was taken on (hash of csrc/lbm_device.cuh + lbm_kernels.cu).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/launches_rt256x256x1024.md: 13.912 GB per launch over 67,108,864 cells
+    "k_collide": {"bytes_per_cell": 207.30, "kernel_sha": "14820b30bafa72b0"},
+}
 
 WORKLOADS = {
     "rt256": dict(W=256, Re=4000.0, desc="Rayleigh-Taylor 256x256x1024, Re=4000, At=0.5, "
