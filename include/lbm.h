@@ -165,6 +165,21 @@ lbm_status lbm_profile(lbm_ctx* ctx, int enable);
 lbm_status lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms,
                             long long* launches);
 
+/* FP64 sum of an FP32 device array with no memory allocation: out[0] = sum of
+ * field[0..n-1], out[1] = number of non-finite values, both written to `out`, a device
+ * pointer to 2 doubles.  The paper has no counterpart; this exists for callers that
+ * may not allocate device memory when they need the sum -- code running under a fixed,
+ * pre-planned memory budget, or inside a framework that forbids cudaMalloc/cudaFree
+ * and allocating library calls on its hot path.  It calls none of them: its scratch is
+ * a 16 KiB array compiled into the library (held on every GPU that loads it until the
+ * process exits).  n must lie in [0, 2^31 - 1], else LBM_EINVAL with a message in
+ * lbm_last_error(NULL).  Asynchronous on `cuda_stream`.  The first call on each device
+ * looks up the scratch address on that device; make that first call before any stream
+ * capture.  All calls on a device share the scratch, so calls that overlap on the GPU
+ * (other streams, other host threads) race and give wrong sums; serialise them. */
+lbm_status lbm_field_sum_noalloc(const float* field, long long n, double* out,
+                                 void* cuda_stream);
+
 /* Release all device memory of the context and the context itself. */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 

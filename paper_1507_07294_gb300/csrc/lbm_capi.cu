@@ -189,6 +189,8 @@ lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, std::vector
 
 }  // namespace
 
+void lbm::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_allocator* alloc,

@@ -3,9 +3,14 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// Message returned by lbm_last_error(NULL) (per host thread).
+void set_global_error(const std::string& msg);
 
 // Upper bound on the number of per-block partial sums of the FP64 reduction.
 constexpr int kReduceMaxParts = 1024;

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "lbm_get_step": (c_int, [c_void_p, POINTER(c_longlong)]),
     "lbm_profile": (c_int, [c_void_p, c_int]),
     "lbm_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_longlong)]),
+    "lbm_field_sum_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_void_p]),
     "lbm_destroy": (c_int, [c_void_p]),
     "lbm_last_error": (c_char_p, [c_void_p]),
 }
@@ -283,6 +284,16 @@ def lbm_profile_read(ctx: Context, kernel: int):
     _check(lib, lib.lbm_profile_read(ctx.handle, kernel, ctypes.byref(ms), ctypes.byref(n)),
            ctx.handle)
     return ms.value, n.value
+
+
+def lbm_field_sum_noalloc(field_ptr: int, n: int, out_ptr: int, stream: Optional[int] = None) -> None:
+    """lbm_field_sum_noalloc on device pointers (e.g. torch tensors' data_ptr())."""
+    lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib, lib.lbm_field_sum_noalloc(c_void_p(field_ptr), int(n), c_void_p(out_ptr),
+                                          c_void_p(stream)), None)
 
 
 def lbm_destroy(ctx: Context) -> None:
