@@ -42,11 +42,14 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
 }
 
 // ------------------------------------------------------------------- k_mu ---------
-// Shared-memory tiling of the 15-point stencil: a block computes a kTX x kTY x kTZ
-// brick of cells from one load of the brick plus a one-cell halo, so each phi value is
-// read from global memory about (kTX+2)(kTY+2)(kTZ+2)/(kTX kTY kTZ) = 1.7 times
-// instead of 15 times, and all of a thread's loads are in flight together.
-constexpr int kTX = 32, kTY = 8, kTZ = 8;
+// Shared-memory tiling of the 15-point stencil: a block of kTX x kTY threads computes a
+// kTX x kTY x kTZ brick of cells from one load of the brick plus a one-cell halo, so
+// each phi value is read from global memory (kTX+2)(kTY+2)(kTZ+2)/(kTX kTY kTZ) = 1.5
+// times instead of 15 times.  The halo is loaded row by row (one address computation
+// per row of kTX + 2 values), and each thread walks its column in z keeping, per plane,
+// the centre, the sum of the 4 in-plane face neighbours and the sum of the 4 in-plane
+// diagonal neighbours, so every plane is summed once for the three cells that use it.
+constexpr int kTX = 32, kTY = 8, kTZ = 16;
 constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;
 
 // v mod n for v in [-1, n + span): a compare and add when n >= span, else a modulo.
@@ -61,33 +64,44 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
                                                  Physics ph) {
   __shared__ float tile[kHZ][kHY][kHX];
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
-  const int tid = threadIdx.y * kTX + threadIdx.x;
-  // brick + halo; x, y wrap; z wraps or, between walls, clamps (ghost = adjacent node)
-  for (int k = tid; k < kHX * kHY * kHZ; k += kTX * kTY) {
-    const int j = k % kHX, i = (k / kHX) % kHY, l = k / (kHX * kHY);
-    const int gx = wrap(x0 - 1 + j, geo.nx, kHX), gy = wrap(y0 - 1 + i, geo.ny, kHY);
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  // columns of the halo brick this lane loads: j = lane and, for lanes 0-1, j = 32 + lane
+  const int gx_a = wrap(x0 - 1 + lane, geo.nx, kHX);
+  const int gx_b = wrap(x0 - 1 + kTX + (lane & 1), geo.nx, kHX);
+  for (int r = warp; r < kHZ * kHY; r += kTY) {
+    const int l = r / kHY, i = r - l * kHY;
+    const int gy = wrap(y0 - 1 + i, geo.ny, kHY);
     const int zz = z0 - 1 + l;
     const int gz = geo.walls ? min(max(zz, 0), geo.nz - 1) : wrap(zz, geo.nz, kHZ);
-    tile[l][i][j] = __ldg(phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx + gx);
+    const float* row = phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx;
+    tile[l][i][lane] = __ldg(row + gx_a);
+    if (lane < 2) tile[l][i][kTX + lane] = __ldg(row + gx_b);
   }
   __syncthreads();
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const int x = x0 + lane, y = y0 + warp;
   if (x >= geo.nx || y >= geo.ny) return;
-  const int i = threadIdx.y + 1, j = threadIdx.x + 1;
-  for (int l = 1; l <= kTZ && z0 + l - 1 < geo.nz; ++l) {
-    Stencil s;
-    s.c = tile[l][i][j];
-    s.xm = tile[l][i][j - 1];
-    s.xp = tile[l][i][j + 1];
-    s.ym = tile[l][i - 1][j];
-    s.yp = tile[l][i + 1][j];
-    s.zm = tile[l - 1][i][j];
-    s.zp = tile[l + 1][i][j];
-#pragma unroll
-    for (int b = 0; b < 8; ++b)
-      s.k[b] = tile[(b & 4) ? l + 1 : l - 1][(b & 2) ? i + 1 : i - 1][(b & 1) ? j + 1 : j - 1];
-    const int z = z0 + l - 1;
-    mu[(static_cast<size_t>(z) * geo.ny + y) * geo.nx + x] = chemical_potential(ph, s.c, stencil_lap(s));
+  const int i = warp + 1, j = lane + 1;
+  // per-plane partial sums of column (i, j): centre, faces, diagonals
+  auto plane = [&](int l, float& c, float& f, float& d) {
+    c = tile[l][i][j];
+    f = (tile[l][i][j - 1] + tile[l][i][j + 1]) + (tile[l][i - 1][j] + tile[l][i + 1][j]);
+    d = (tile[l][i - 1][j - 1] + tile[l][i - 1][j + 1]) + (tile[l][i + 1][j - 1] + tile[l][i + 1][j + 1]);
+  };
+  float c0, f0, d0, c1, f1, d1;
+  plane(0, c0, f0, d0);
+  plane(1, c1, f1, d1);
+  const int nl = min(kTZ, geo.nz - z0);
+  float* out = mu + (static_cast<size_t>(z0) * geo.ny + y) * geo.nx + x;
+  const size_t zstride = static_cast<size_t>(geo.plane);
+  for (int l = 1; l <= nl; ++l) {
+    float c2, f2, d2;
+    plane(l + 1, c2, f2, d2);
+    // Eq. 36 on the D3Q15 stencil: 2/3 (faces - 6 c) + 1/12 (corners - 8 c)
+    const float lap = (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
+                      (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
+    out[(l - 1) * zstride] = chemical_potential(ph, c1, lap);
+    c0 = c1; f0 = f1; d0 = d1;
+    c1 = c2; f1 = f2; d1 = d2;
   }
 }
 
