@@ -191,6 +191,40 @@ def dist_env():
     return world, rank, local
 
 
+class RankGroup:
+    """The host-side collectives of the benchmark: a barrier and a max over ranks.
+
+    Each rank runs an independent replica, so these are the only collectives; they
+    are used for timing, never on the data path.  backend "nccl" reduces a CUDA tensor,
+    "gloo" a CPU one; with one rank both are no-ops.
+    """
+
+    def __init__(self, world: int, rank: int, backend: str = "nccl"):
+        self.world, self.rank, self.backend = world, rank, backend
+
+    def _device(self):
+        return "cuda" if self.backend == "nccl" else "cpu"
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return float(x)
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self._device())
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def aggregate_mlups(cells: int, steps: int, world: int, elapsed_s: float) -> float:
+    """Whole-job MLUPS: the cell updates of all replicas over the slowest rank's time."""
+    return cells * steps * world / elapsed_s / 1e6
+
+
 def config_dict(args, w, world):
     spec = WORKLOADS[args.workload]
     return {"workload": f"{args.workload}: {spec['desc']}",
@@ -254,18 +288,14 @@ def run_ours(args):
     solver = L.Solver(w, stream=stream.cuda_stream, pattern=args.pattern)
     ctx = solver.ctx
 
+    group = RankGroup(world, rank, "nccl")
+
     def barrier():
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        group.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = group.max
 
     # ---- device-timed region -------------------------------------------------
     solver.step(args.warmup)
@@ -291,7 +321,7 @@ def run_ours(args):
     sum_phi, _ = solver.reduce()  # the run stayed finite
 
     cells = w.cells
-    value = cells * args.steps * world / (elapsed_ms * 1e-3) / 1e6
+    value = aggregate_mlups(cells, args.steps, world, elapsed_ms * 1e-3)
     coll_ms = kernels["k_collide"]["mean_ms"]
     peak, peak_kind = measured_peaks()
     achieved = COLLIDE_BYTES_PER_CELL * cells / (coll_ms * 1e-3) / 1e9
@@ -314,7 +344,7 @@ def run_ours(args):
         barrier()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         assert np.isfinite(out["phi"]).all()
-        e2e = {"value": round(cells * args.steps * world / t_e2e / 1e6, 3), "unit": UNIT,
+        e2e = {"value": round(aggregate_mlups(cells, args.steps, world, t_e2e), 3), "unit": UNIT,
                "h2d_bytes_per_step": round(8 * cells / args.steps),
                "d2h_bytes_per_step": round(5 * 8 + 5 * 4 * cells / args.steps),
                "seconds": round(t_e2e, 4)}
