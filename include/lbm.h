@@ -121,6 +121,24 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
  * earlier value).  Synchronises the stream. */
 lbm_status lbm_init_phi(lbm_ctx* ctx, const double* phi, const double* u, const double* p);
 
+/* Prescribed velocity fields for lbm_set_velocity. */
+#define LBM_VELOCITY_NONE 0        /* coupled: u from the flow lattice (default)        */
+#define LBM_VELOCITY_UNIFORM 1     /* u = (U, 0, 0)                                      */
+#define LBM_VELOCITY_ROTATION 2    /* Eq. 37: rigid rotation about the x axis through the
+                                      box centre, Omega = U pi / ny (one turn in 2 ny / U
+                                      steps)                                             */
+#define LBM_VELOCITY_DEFORMATION 3 /* Eq. 41 with L = nx, times cos(pi t / period), t the
+                                      step count                                         */
+
+/* Interface-tracking mode (Sec. III A, B): with kind != LBM_VELOCITY_NONE only the D3Q7
+ * lattice evolves (Eq. 4) and u is the prescribed field, evaluated at the integer node
+ * coordinates of the (periodic) box; the flow lattice is not used (lbm_reduce reports
+ * zero momentum, lbm_read_fields a zero pressure and the prescribed u).  Call before
+ * lbm_init_phi, which then starts f from f^eq with the field's u at t = 0 (the u
+ * argument is ignored).  LBM_EINVAL for an unknown kind or, for the deformation field, a
+ * period <= 0. */
+lbm_status lbm_set_velocity(lbm_ctx* ctx, int kind, double U, double period);
+
 /* Advance n >= 0 time steps (Eqs. 4 and 20: stream, then collide in moment space with
  * Eqs. 17-18 and 31-32).  Asynchronous on the context's stream. */
 lbm_status lbm_step(lbm_ctx* ctx, int n);

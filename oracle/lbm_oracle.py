@@ -331,6 +331,52 @@ def stream(post: np.ndarray, C: np.ndarray, opp: np.ndarray, walls_z: bool) -> n
 
 
 # ----------------------------------------------------------------------------------
+# Prescribed velocity fields of the interface-tracking tests (Sec. III A, B)
+# ----------------------------------------------------------------------------------
+
+def prescribed_velocity(kind: str, U: float, period: float, box, t: float,
+                        coords=None) -> np.ndarray:
+    """u(x, t) at the nodes x_i = i of a periodic box of size box = (NZ, NY, NX).
+
+    "uniform": u = (U, 0, 0).
+    "rotation" (Eq. 37): rigid rotation about the x axis through the box centre,
+        v = -Omega (z - N/2), w = Omega (y - N/2), Omega = U pi / N with N = NY (the
+        paper's 100^3 case: Omega = U pi / 100, one turn in 200/U steps); `period` unused.
+    "deformation" (Eq. 41): with L = NX and the time factor cos(pi t / period),
+        u = 2U sin^2(pi x/L) sin(2 pi y/L) sin(2 pi z/L),
+        v = -U sin(2 pi x/L) sin^2(pi y/L) sin(2 pi z/L),
+        w = -U sin(2 pi x/L) sin(2 pi y/L) sin^2(pi z/L).
+    coords: optional (z, y, x) index arrays (broadcastable) of the nodes to evaluate;
+    default the whole box.
+    """
+    NZ, NY, NX = box
+    if coords is None:
+        z, y, x = np.meshgrid(np.arange(NZ, dtype=np.float64), np.arange(NY, dtype=np.float64),
+                              np.arange(NX, dtype=np.float64), indexing="ij")
+    else:
+        z, y, x = (np.asarray(c, dtype=np.float64) for c in coords)
+        z, y, x = np.broadcast_arrays(z, y, x)
+    u = np.zeros((3,) + z.shape)
+    if kind == "uniform":
+        u[0] = U
+    elif kind == "rotation":
+        omega = U * np.pi / NY
+        u[1] = -omega * (z - NY / 2.0)
+        u[2] = omega * (y - NY / 2.0)
+    elif kind == "deformation":
+        L = float(NX)
+        a = np.cos(np.pi * t / period)
+        sx, sy, sz = np.sin(np.pi * x / L), np.sin(np.pi * y / L), np.sin(np.pi * z / L)
+        s2x, s2y, s2z = np.sin(2 * np.pi * x / L), np.sin(2 * np.pi * y / L), np.sin(2 * np.pi * z / L)
+        u[0] = 2.0 * U * sx * sx * s2y * s2z * a
+        u[1] = -U * s2x * sy * sy * s2z * a
+        u[2] = -U * s2x * s2y * sz * sz * a
+    else:
+        raise ValueError(kind)
+    return u
+
+
+# ----------------------------------------------------------------------------------
 # The coupled solver
 # ----------------------------------------------------------------------------------
 
@@ -354,6 +400,9 @@ class Params:
     sf: Sequence[float] = (1.0, 1.25, 1.25, 1.25, 1.2, 1.0, 1.0)
     sg: Sequence[float] = (1.0,) * 15
     buoyancy: bool = False
+    # interface tracking with a prescribed velocity instead of the flow lattice:
+    # None (coupled), ("rotation", U) or ("deformation", U, period_in_steps)
+    velocity: Optional[tuple] = None
 
     @property
     def kappa(self):
@@ -380,7 +429,7 @@ class Params:
         return cls(nx=w.nx, ny=w.ny, nz=w.nz, walls_z=bool(w.walls_z), rho_l=w.rho_l,
                    rho_g=w.rho_g, nu_l=w.nu_l, nu_g=w.nu_g, mobility=w.mobility, D=w.D,
                    sigma=w.sigma, g=tuple(w.g), A=w.A, sf=tuple(w.sf), sg=tuple(w.sg),
-                   buoyancy=bool(w.buoyancy))
+                   buoyancy=bool(w.buoyancy), velocity=getattr(w, "velocity", None))
 
 
 class Oracle:
@@ -388,12 +437,19 @@ class Oracle:
 
     State between steps: the populations f (7) and g (15) at time t just after
     propagation, the product phi u of the previous step, and the step count.
+
+    With params.velocity set, only the interface lattice evolves (Eq. 4) and u is the
+    prescribed field of Eq. 37 or Eq. 41 (Sec. III A, B); g is not used.
     """
 
-    def __init__(self, params: Params):
+    def __init__(self, params: Params, box=None, coords=None):
+        """box, coords: for a patch cut out of a larger grid, the full box size and the
+        global (z, y, x) indices of the patch's nodes (used by the prescribed velocity)."""
         if not (params.sf[1] == params.sf[2] == params.sf[3]):
             raise ValueError("Eq. 19 needs s_1 = s_2 = s_3")
         self.p = params
+        self.box = box if box is not None else (params.nz, params.ny, params.nx)
+        self.coords = coords
         self.f: Optional[np.ndarray] = None
         self.g: Optional[np.ndarray] = None
         self.phiu_prev: Optional[np.ndarray] = None
@@ -406,6 +462,11 @@ class Oracle:
             return (rho - 0.5 * (self.p.rho_l + self.p.rho_g))[None] * gv
         return rho[None] * gv
 
+    def _prescribed(self):
+        v = self.p.velocity
+        period = v[2] if len(v) > 2 else 1.0
+        return prescribed_velocity(v[0], v[1], period, self.box, self.t, self.coords)
+
     def macroscopic(self):
         """All macroscopic fields at the current time from the current populations."""
         p = self.p
@@ -413,6 +474,8 @@ class Oracle:
         phi = order_parameter(self.f)
         rho = density(phi, p.rho_l, p.rho_g)
         mu = chemical_potential(phi, lap_iso(phi, wz), p.beta, p.kappa)
+        if p.velocity is not None:
+            return dict(phi=phi, rho=rho, mu=mu, u=self._prescribed(), p=np.zeros_like(phi))
         grad_phi = grad_iso(phi, wz)
         grad_rho = grad_iso(rho, wz)
         lap_mu = lap_iso(mu, wz)
@@ -434,10 +497,12 @@ class Oracle:
         p0 = np.zeros(shape) if p0 is None else np.asarray(p0, np.float64).reshape(shape)
         mu0 = chemical_potential(phi0, lap_iso(phi0, p.walls_z), p.beta, p.kappa)
         rho0 = density(phi0, p.rho_l, p.rho_g)
+        self.t = 0
+        if p.velocity is not None:
+            u0 = self._prescribed()
         self.f = d3q7_feq(phi0, mu0, u0, p.eta, p.A)
         self.g = d3q15_geq(p0, rho0, u0)
         self.phiu_prev = None
-        self.t = 0
 
     def step(self, n: int = 1):
         for _ in range(n):
@@ -449,13 +514,15 @@ class Oracle:
         phi, rho, u = mac["phi"], mac["rho"], mac["u"]
 
         # Flow lattice: collision in moment space (Eqs. 20, 27, 31, 32).
-        rates_g = np.broadcast_to(np.asarray(p.sg, np.float64).reshape(15, 1, 1, 1),
-                                  (15,) + phi.shape).copy()
-        rates_g[9:14] = p.viscous_rate(phi)[None]
-        mg = to_moments(GAMMA, self.g)
-        mg_post = collide_moments(mg, d3q15_mgeq(mac["p"], rho, u), rates_g,
-                                  d3q15_mT(u, mac["grad_rho"], mac["F"]))
-        g_post = to_moments(GAMMA_INV, mg_post)
+        g_post = None
+        if p.velocity is None:
+            rates_g = np.broadcast_to(np.asarray(p.sg, np.float64).reshape(15, 1, 1, 1),
+                                      (15,) + phi.shape).copy()
+            rates_g[9:14] = p.viscous_rate(phi)[None]
+            mg = to_moments(GAMMA, self.g)
+            mg_post = collide_moments(mg, d3q15_mgeq(mac["p"], rho, u), rates_g,
+                                      d3q15_mT(u, mac["grad_rho"], mac["F"]))
+            g_post = to_moments(GAMMA_INV, mg_post)
 
         # Interface lattice: backward time difference (Eq. 34), collision (Eqs. 15-18).
         phiu = phi[None] * u
@@ -469,7 +536,8 @@ class Oracle:
 
         # Propagation (Eq. 16).
         self.f = stream(f_post, D3Q7_C, OPP7, p.walls_z)
-        self.g = stream(g_post, D3Q15_C, OPP15, p.walls_z)
+        if g_post is not None:
+            self.g = stream(g_post, D3Q15_C, OPP15, p.walls_z)
         self.t += 1
 
     def fields(self):

@@ -31,6 +31,10 @@ struct lbm_ctx {
   double* partial = nullptr;  // reduction partials
   double* red = nullptr;      // 5 reduction results
 
+  // interface-tracking mode (0: coupled): prescribed velocity kind, amplitude, period
+  int vel_kind = 0;
+  double vel_U = 0.0, vel_period = 1.0;
+
   long long step = 0;
   bool odd = false;        // parity of the stored populations (pattern AA)
   bool have_prev = false;  // phiu holds the previous step's phi u
@@ -162,6 +166,13 @@ int read_pattern(const lbm_ctx* c) {
 
 float* cur_state(lbm_ctx* c) { return c->pop[c->cur]; }
 
+// Time factor of the prescribed velocity at step t: cos(pi t / T) for the deformation
+// field (Eq. 41), 1 otherwise; evaluated in double on the host.
+float velocity_time_factor(const lbm_ctx* c, long long t) {
+  if (c->vel_kind != LBM_VELOCITY_DEFORMATION) return 1.0f;
+  return static_cast<float>(std::cos(3.14159265358979323846 * static_cast<double>(t) / c->vel_period));
+}
+
 template <typename F>
 cudaError_t timed(lbm_ctx* c, int kernel, F&& launch) {
   if (!c->profiling) return launch();
@@ -270,7 +281,8 @@ lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const do
   c->odd = false;
   if (e == cudaSuccess)
     e = lbm::launch_init(cur_state(c), c->phi, c->mu, u ? c->stage : nullptr,
-                         p ? c->stage + 3 * s : nullptr, c->geo, c->ph, read_pattern(c), c->stream);
+                         p ? c->stage + 3 * s : nullptr, c->geo, c->ph, read_pattern(c),
+                         velocity_time_factor(c, 0), c->stream);
   const cudaError_t es = cudaStreamSynchronize(c->stream);
   dev_free(c, tmp);
   if (e != cudaSuccess) return fail_cuda(c, "lbm_init_phi", e);
@@ -292,10 +304,18 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->geo, pat, c->stream); }));
     LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
     const bool prev = c->have_prev;
-    LBM_CK(c, timed(c, 2, [&] {
-             return lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev,
-                                        c->stream);
-           }));
+    if (c->vel_kind == LBM_VELOCITY_NONE) {
+      LBM_CK(c, timed(c, 2, [&] {
+               return lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev,
+                                          c->stream);
+             }));
+    } else {
+      const float tf = velocity_time_factor(c, c->step);
+      LBM_CK(c, timed(c, 2, [&] {
+               return lbm::launch_che(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev, tf,
+                                      c->stream);
+             }));
+    }
     if (c->params.pattern == LBM_PATTERN_AB)
       c->cur = 1 - c->cur;
     else
@@ -317,7 +337,7 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   LBM_CK(c, lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream));
   if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
     LBM_CK(c, lbm::launch_fields(cur_state(c), c->phi, c->mu, c->stage, c->geo, c->ph,
-                                 read_pattern(c), c->stream));
+                                 read_pattern(c), velocity_time_factor(c, c->step), c->stream));
   const size_t n = static_cast<size_t>(c->geo.n);
   const size_t s = c->geo.stride;
   std::vector<float> tmp;
@@ -338,7 +358,7 @@ lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
   LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, c->geo, read_pattern(c), c->stream));
   LBM_CK(c, lbm::launch_reduce(cur_state(c), c->phi, c->partial, c->red, c->geo, read_pattern(c),
-                               c->stream));
+                               c->vel_kind == LBM_VELOCITY_NONE, c->stream));
   double h[5];
   LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
@@ -398,6 +418,21 @@ lbm_status lbm_write_state(lbm_ctx* c, const float* f, const float* g, const flo
   c->have_prev = prev;
   c->step = step;
   c->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_velocity(lbm_ctx* c, int kind, double U, double period) {
+  if (!c) return LBM_EINVAL;
+  if (kind < LBM_VELOCITY_NONE || kind > LBM_VELOCITY_DEFORMATION)
+    return fail(c, LBM_EINVAL, "unknown velocity kind");
+  if (!std::isfinite(U)) return fail(c, LBM_EINVAL, "U must be finite");
+  if (kind == LBM_VELOCITY_DEFORMATION && !(period > 0 && std::isfinite(period)))
+    return fail(c, LBM_EINVAL, "the deformation field needs a period > 0");
+  c->vel_kind = kind;
+  c->vel_U = U;
+  c->vel_period = kind == LBM_VELOCITY_DEFORMATION ? period : 1.0;
+  c->ph.vel_kind = kind;
+  c->ph.vel_U = static_cast<float>(U);
   return LBM_OK;
 }
 

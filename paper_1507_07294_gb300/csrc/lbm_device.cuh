@@ -47,7 +47,12 @@ struct Physics {
   float rho_ref;     // G = (rho - rho_ref) g; 0 for the plain weight
   float sf[7];       // S^f (Eq. 10)
   float sg[15];      // S^g (Eq. 26), entries 9..13 unused (viscous, per cell)
+  int vel_kind;      // 0: coupled; else the prescribed velocity field (VelocityKind)
+  float vel_U;       // its amplitude U
 };
+
+// Prescribed velocity fields of the interface-tracking mode (Sec. III A, B).
+enum VelocityKind { kVelNone = 0, kVelUniform = 1, kVelRotation = 2, kVelDeformation = 3 };
 
 // Population q of the D3Q7 set lives at slot q (0..6), population i of the D3Q15
 // set at slot 7 + i, and the three components of phi u of the previous step at slots
@@ -295,6 +300,37 @@ __device__ __forceinline__ void stencil_grad(const Stencil& s, float g[3]) {
   g[0] = (1.0f / 3.0f) * (s.xp - s.xm) + (1.0f / 24.0f) * kx;
   g[1] = (1.0f / 3.0f) * (s.yp - s.ym) + (1.0f / 24.0f) * ky;
   g[2] = (1.0f / 3.0f) * (s.zp - s.zm) + (1.0f / 24.0f) * kz;
+}
+
+// u(x, t) of the interface-tracking tests at node (x, y, z) (nodes at integer
+// coordinates of a periodic box); tf is the time factor (cos(pi t / T) for the
+// deformation field, 1 otherwise).
+//   uniform:     (U, 0, 0)
+//   rotation:    Eq. 37, v = -Omega (z - N/2), w = Omega (y - N/2), Omega = U pi / N, N = ny
+//   deformation: Eq. 41 with L = nx.
+__device__ __forceinline__ void prescribed_velocity(const Physics& ph, const Geometry& geo, int x,
+                                                    int y, int z, float tf, float u[3]) {
+  const float U = ph.vel_U;
+  if (ph.vel_kind == kVelUniform) {
+    u[0] = U;
+    u[1] = 0.0f;
+    u[2] = 0.0f;
+  } else if (ph.vel_kind == kVelRotation) {
+    const float omega = U * 3.14159265358979f / static_cast<float>(geo.ny);
+    const float c = 0.5f * static_cast<float>(geo.ny);
+    u[0] = 0.0f;
+    u[1] = -omega * (static_cast<float>(z) - c);
+    u[2] = omega * (static_cast<float>(y) - c);
+  } else {
+    const float inv_l = 1.0f / static_cast<float>(geo.nx);
+    const float ax = static_cast<float>(x) * inv_l, ay = static_cast<float>(y) * inv_l,
+                az = static_cast<float>(z) * inv_l;
+    const float sx = sinpif(ax), sy = sinpif(ay), sz = sinpif(az);
+    const float s2x = sinpif(2.0f * ax), s2y = sinpif(2.0f * ay), s2z = sinpif(2.0f * az);
+    u[0] = 2.0f * U * sx * sx * s2y * s2z * tf;
+    u[1] = -U * s2x * sy * sy * s2z * tf;
+    u[2] = -U * s2x * s2y * sz * sz * tf;
+  }
 }
 
 // mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2).

@@ -22,11 +22,15 @@ cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Ph
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
                            const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                            cudaStream_t st);
+cudaError_t launch_che(const float* src, float* dst, const float* phi, const float* mu,
+                       const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
+                       float tf, cudaStream_t st);
 cudaError_t launch_fields(const float* src, const float* phi, const float* mu, float* out,
-                          const Geometry& geo, const Physics& ph, int pattern, cudaStream_t st);
+                          const Geometry& geo, const Physics& ph, int pattern, float tf,
+                          cudaStream_t st);
 cudaError_t launch_init(float* state, const float* phi, const float* mu, const float* u0,
                         const float* p0, const Geometry& geo, const Physics& ph, int pattern,
-                        cudaStream_t st);
+                        float tf, cudaStream_t st);
 cudaError_t launch_gather(const float* src, float* dense, const Geometry& geo, int pattern,
                           int slot, cudaStream_t st);
 cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
@@ -34,7 +38,7 @@ cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
 cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
-                          const Geometry& geo, int pattern, cudaStream_t st);
+                          const Geometry& geo, int pattern, bool with_g, cudaStream_t st);
 // Floats of the tiled cell-state array for n cells.
 inline size_t state_floats(int n) {
   return static_cast<size_t>((n + kTile - 1) / kTile) * kTileSlots * kTile;

@@ -171,6 +171,39 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
   store_f<P>(dst, idx, nb, f);
 }
 
+// ------------------------------------------------------------------ k_che ---------
+// Interface tracking with a prescribed velocity (Sec. III A, B): only the D3Q7 lattice
+// evolves (Eq. 4); u is analytic, so the flow lattice and the stencils of phi and mu
+// are not needed.  tf is the time factor of the velocity field at this step.
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_che(const float* src, float* dst,
+                                                const float* __restrict__ phi,
+                                                const float* __restrict__ mu, Geometry geo,
+                                                Physics ph, int have_prev, float tf) {
+  const int idx = blockIdx.x * kBlock + threadIdx.x;
+  if (idx >= geo.n) return;
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
+  float f[7], prev[3];
+  load_f<P>(src, idx, nb, f);
+  const size_t own = tile_base(idx) + kSlotPhiu * kTile;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) prev[a] = src[own + a * kTile];
+  const float phi_c = __ldg(phi + idx), mu_c = __ldg(mu + idx);
+  float u[3];
+  prescribed_velocity(ph, geo, x, y, z, tf, u);
+  float dphiu[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float cur = phi_c * u[a];
+    dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
+    dst[own + a * kTile] = cur;
+  }
+  collide_d3q7(ph, f, phi_c, mu_c, u, dphiu);
+  store_f<P>(dst, idx, nb, f);
+}
+
 // --------------------------------------------------------------- k_fields ---------
 // rho, p, u of the current populations into out[0..4] (rho, p, ux, uy, uz).
 template <int P>
@@ -178,17 +211,27 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src
                                                    const float* __restrict__ phi,
                                                    const float* __restrict__ mu,
                                                    float* __restrict__ out, Geometry geo,
-                                                   Physics ph) {
+                                                   Physics ph, float tf) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
   int x, y, z;
   cell_coords(geo, idx, x, y, z);
+  const size_t s = geo.stride;
+  if (ph.vel_kind != kVelNone) {  // tracking mode: prescribed u, no pressure
+    float u[3];
+    prescribed_velocity(ph, geo, x, y, z, tf, u);
+    out[0 * s + idx] = ph.rho_g + (1.0f + __ldg(phi + idx)) * ph.half_drho;
+    out[1 * s + idx] = 0.0f;
+    out[2 * s + idx] = u[0];
+    out[3 * s + idx] = u[1];
+    out[4 * s + idx] = u[2];
+    return;
+  }
   const Nbr nb = make_nbr(geo, x, y, z);
   const CellStencils cs = cell_stencils(phi, mu, idx, nb);
   float g[15];
   load_g<P>(src, idx, nb, g);
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
-  const size_t s = geo.stride;
   out[0 * s + idx] = M.rho;
   out[1 * s + idx] = M.p;
   out[2 * s + idx] = M.u[0];
@@ -204,7 +247,7 @@ __global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __re
                                                  const float* __restrict__ mu,
                                                  const float* __restrict__ u0,
                                                  const float* __restrict__ p0, Geometry geo,
-                                                 Physics ph) {
+                                                 Physics ph, float tf) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
   int x, y, z;
@@ -213,7 +256,9 @@ __global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __re
   const size_t s = geo.stride;
   const float ph_ = phi[idx], mu_ = mu[idx];
   float u[3] = {0.0f, 0.0f, 0.0f};
-  if (u0) {
+  if (ph.vel_kind != kVelNone) {
+    prescribed_velocity(ph, geo, x, y, z, tf, u);
+  } else if (u0) {
     u[0] = u0[idx];
     u[1] = u0[s + idx];
     u[2] = u0[2 * s + idx];
@@ -319,22 +364,26 @@ __global__ void __launch_bounds__(kBlock) k_convert(const double* __restrict__ i
 // Pass 1: block b sums cells b*256 + t, then strides by the grid, in FP64 (fixed
 // order: grid-stride rows, then a fixed shuffle tree).
 // partial[b] = {sum phi, jx, jy, jz, non-finite count}.
+// with_g = 0 (tracking mode, no flow lattice): the momentum sums are zero.
 template <int P>
 __global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restrict__ src,
                                                            const float* __restrict__ phi,
                                                            double* __restrict__ partial,
-                                                           Geometry geo) {
+                                                           Geometry geo, int with_g) {
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int idx = blockIdx.x * kBlock + threadIdx.x; idx < geo.n; idx += gridDim.x * kBlock) {
-    int x, y, z;
-    cell_coords(geo, idx, x, y, z);
-    const Nbr nb = make_nbr(geo, x, y, z);
-    float g[15];
-    load_g<P>(src, idx, nb, g);
-    const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12], d13 = g[13] - g[14];
-    const float jx = (g[1] - g[2]) + ((d7 + d9) + (d11 + d13));
-    const float jy = (g[3] - g[4]) + ((d7 + d9) - (d11 + d13));
-    const float jz = (g[5] - g[6]) + ((d7 - d9) + (d11 - d13));
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    if (with_g) {
+      int x, y, z;
+      cell_coords(geo, idx, x, y, z);
+      const Nbr nb = make_nbr(geo, x, y, z);
+      float g[15];
+      load_g<P>(src, idx, nb, g);
+      const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12], d13 = g[13] - g[14];
+      jx = (g[1] - g[2]) + ((d7 + d9) + (d11 + d13));
+      jy = (g[3] - g[4]) + ((d7 + d9) - (d11 + d13));
+      jz = (g[5] - g[6]) + ((d7 - d9) + (d11 - d13));
+    }
     const float p = phi[idx];
     acc[0] += p;
     acc[1] += jx;
@@ -412,16 +461,24 @@ cudaError_t launch_collide(const float* src, float* dst, const float* phi, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_che(const float* src, float* dst, const float* phi, const float* mu,
+                       const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
+                       float tf, cudaStream_t st) {
+  LBM_DISPATCH(pattern, k_che, src, dst, phi, mu, geo, ph, have_prev ? 1 : 0, tf);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fields(const float* src, const float* phi, const float* mu, float* out,
-                          const Geometry& geo, const Physics& ph, int pattern, cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_fields, src, phi, mu, out, geo, ph);
+                          const Geometry& geo, const Physics& ph, int pattern, float tf,
+                          cudaStream_t st) {
+  LBM_DISPATCH(pattern, k_fields, src, phi, mu, out, geo, ph, tf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_init(float* state, const float* phi, const float* mu, const float* u0,
                         const float* p0, const Geometry& geo, const Physics& ph, int pattern,
-                        cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_init, state, phi, mu, u0, p0, geo, ph);
+                        float tf, cudaStream_t st) {
+  LBM_DISPATCH(pattern, k_init, state, phi, mu, u0, p0, geo, ph, tf);
   return cudaGetLastError();
 }
 
@@ -448,14 +505,15 @@ int reduce_parts(const Geometry& geo) {
 }
 
 cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
-                          const Geometry& geo, int pattern, cudaStream_t st) {
+                          const Geometry& geo, int pattern, bool with_g, cudaStream_t st) {
   const int parts = reduce_parts(geo);
+  const int wg = with_g ? 1 : 0;
   if (pattern == kAB)
-    k_reduce_partial<kAB><<<parts, kBlock, 0, st>>>(src, phi, partial, geo);
+    k_reduce_partial<kAB><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
   else if (pattern == kAAEven)
-    k_reduce_partial<kAAEven><<<parts, kBlock, 0, st>>>(src, phi, partial, geo);
+    k_reduce_partial<kAAEven><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
   else
-    k_reduce_partial<kAAOdd><<<parts, kBlock, 0, st>>>(src, phi, partial, geo);
+    k_reduce_partial<kAAOdd><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_final<<<1, kBlock, 0, st>>>(partial, parts, out);

@@ -55,6 +55,9 @@ class Workload:
     buoyancy: bool = False
     steps: int = 100
     U: float = 1.0  # velocity scale used to normalise velocity errors
+    # interface tracking with a prescribed velocity (no flow lattice):
+    # None, ("uniform", U), ("rotation", U) or ("deformation", U, period_in_steps)
+    velocity: Optional[tuple] = None
     phi0: Optional[np.ndarray] = field(default=None, repr=False)
     u0: Optional[np.ndarray] = field(default=None, repr=False)
     p0: Optional[np.ndarray] = field(default=None, repr=False)
@@ -129,6 +132,62 @@ def flat_interface(nz: int = 32, nxy: int = 4, D: float = 4.0, sigma: float = 0.
                     rho_l=rho_l, rho_g=rho_g, nu_l=nu, nu_g=nu, mobility=mobility, D=D,
                     sigma=sigma, g=(0.0, 0.0, 0.0), sf=SF_COUPLED, steps=steps,
                     U=sigma / (rho_l * nu), phi0=phi0)
+
+
+def deformation(n: int = 128, U: float = 0.02, period: float = 3000.0, D: float = 2.0,
+                sigma: float = 0.04, Pe: float = 400.0) -> Workload:
+    """Deformation-flow test (Sec. III B, Eq. 41) scaled to an n^3 periodic box: sphere of
+    radius 0.15 n centred at 0.35 n in each axis (15 and 35 in the paper's 100^3 box),
+    velocity amplitude U, time factor cos(pi t / period) with t in steps; the mobility
+    from Pe = U R / Mob (Eq. 39 with L = R); S^f of Eq. 38."""
+    R = 0.15 * n
+    c = 0.35 * n
+    x, y, z = node_coords(n, n, n, False)
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    phi0 = np.tanh(2.0 * (R - r) / D)
+    return Workload(name=f"deformation{n}", nx=n, ny=n, nz=n, walls_z=False, rho_l=1.0,
+                    rho_g=1.0, nu_l=0.1, nu_g=0.1, mobility=U * R / Pe, D=D, sigma=sigma,
+                    g=(0.0, 0.0, 0.0), sf=SF_TRACKING, steps=int(period), U=2.0 * U,
+                    velocity=("deformation", U, float(period)), phi0=phi0)
+
+
+def zalesak(n: int = 100, U: float = 0.02, D: float = 2.0, sigma: float = 0.04,
+            Pe: float = 200.0, slot_depth: Optional[float] = None) -> Workload:
+    """Zalesak's slotted sphere (Sec. III A, Eq. 37) scaled to an n^3 periodic box: radius
+    0.4 n at the centre (40 of 100), a slot of width 0.16 n (16 of 100) along x cut from
+    the bottom of the sphere, depth `slot_depth` (the paper gives none; default R, up to
+    the centre).  Rigid rotation about the x axis, one turn in 2n/U steps; Pe = U R / Mob."""
+    R = 0.4 * n
+    half_w = 0.08 * n
+    depth = R if slot_depth is None else slot_depth
+    c = n / 2.0
+    x, y, z = node_coords(n, n, n, False)
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    # signed distance to the slot box {|y - c| <= half_w, z <= c - R + depth} (outside > 0)
+    qy = np.abs(y - c) - half_w
+    qz = z - (c - R + depth)
+    qy, qz = np.broadcast_arrays(qy, qz)
+    outside = np.sqrt(np.maximum(qy, 0) ** 2 + np.maximum(qz, 0) ** 2)
+    inside = np.minimum(np.maximum(qy, qz), 0.0)
+    d_slot = np.broadcast_to(outside + inside, (n, n, n))
+    d = np.minimum(R - r, d_slot)
+    phi0 = np.tanh(2.0 * d / D)
+    return Workload(name=f"zalesak{n}", nx=n, ny=n, nz=n, walls_z=False, rho_l=1.0, rho_g=1.0,
+                    nu_l=0.1, nu_g=0.1, mobility=U * R / Pe, D=D, sigma=sigma,
+                    g=(0.0, 0.0, 0.0), sf=SF_TRACKING, steps=int(round(2 * n / U)), U=U,
+                    velocity=("rotation", U), phi0=np.ascontiguousarray(phi0))
+
+
+def translating_slab(n: int = 64, U: float = 0.02, D: float = 2.0, sigma: float = 0.04,
+                     mobility: float = 0.02) -> Workload:
+    """A slab phi = +1 for n/4 < x < 3n/4 (two tanh interfaces) in a periodic n x 1 x 1
+    box, carried by the uniform velocity (U, 0, 0)."""
+    x = np.arange(n, dtype=np.float64)
+    phi = np.tanh(2.0 * (x - n / 4) / D) - np.tanh(2.0 * (x - 3 * n / 4) / D) - 1.0
+    return Workload(name=f"slab{n}", nx=n, ny=1, nz=1, walls_z=False, rho_l=1.0, rho_g=1.0,
+                    nu_l=0.1, nu_g=0.1, mobility=mobility, D=D, sigma=sigma,
+                    g=(0.0, 0.0, 0.0), sf=SF_TRACKING, steps=int(round(n / U)), U=U,
+                    velocity=("uniform", U), phi0=phi.reshape(1, 1, n))
 
 
 def perturbed(w: Workload, seed: int = 0, phi_amp: float = 0.0, u_amp: float = 0.0,

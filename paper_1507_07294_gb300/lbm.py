@@ -32,6 +32,10 @@ PATTERNS = {"ab": LBM_PATTERN_AB, "aa": LBM_PATTERN_AA}
 LBM_FIELD_PHI, LBM_FIELD_RHO, LBM_FIELD_P, LBM_FIELD_U, LBM_FIELD_MU = 1, 2, 4, 8, 16
 LBM_FIELD_ALL = 31
 
+LBM_VELOCITY_NONE, LBM_VELOCITY_UNIFORM, LBM_VELOCITY_ROTATION, LBM_VELOCITY_DEFORMATION = 0, 1, 2, 3
+VELOCITY_KINDS = {"uniform": LBM_VELOCITY_UNIFORM, "rotation": LBM_VELOCITY_ROTATION,
+                  "deformation": LBM_VELOCITY_DEFORMATION}
+
 KERNEL_PHI, KERNEL_MU, KERNEL_COLLIDE = 0, 1, 2
 KERNEL_NAMES = ("k_phi", "k_mu", "k_collide")
 
@@ -74,6 +78,7 @@ _SIGNATURES = {
     "lbm_read_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_longlong)]),
     "lbm_write_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_longlong]),
     "lbm_get_step": (c_int, [c_void_p, POINTER(c_longlong)]),
+    "lbm_set_velocity": (c_int, [c_void_p, c_int, c_double, c_double]),
     "lbm_profile": (c_int, [c_void_p, c_int]),
     "lbm_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_longlong)]),
     "lbm_field_sum_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_void_p]),
@@ -264,6 +269,14 @@ def lbm_write_state(ctx: Context, f, g, phiu_prev=None, step: int = 0) -> None:
     _check(lib, lib.lbm_write_state(ctx.handle, _ptr(f), _ptr(g), _ptr(phiu), int(step)), ctx.handle)
 
 
+def lbm_set_velocity(ctx: Context, kind, U: float = 0.0, period: float = 1.0) -> None:
+    """Interface-tracking mode: kind "uniform", "rotation", "deformation" (or the C
+    constants); call before lbm_init_phi."""
+    lib = load_library()
+    k = VELOCITY_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib, lib.lbm_set_velocity(ctx.handle, k, float(U), float(period)), ctx.handle)
+
+
 def lbm_get_step(ctx: Context) -> int:
     lib = load_library()
     s = c_longlong()
@@ -323,6 +336,9 @@ class Solver:
         self.workload = workload
         grid, params = params_from_workload(workload, pattern)
         self.ctx = lbm_create(grid, params, stream=stream, allocator=allocator)
+        v = getattr(workload, "velocity", None)
+        if v is not None:
+            lbm_set_velocity(self.ctx, v[0], v[1], v[2] if len(v) > 2 else 1.0)
         if init:
             lbm_init_phi(self.ctx, workload.phi0, workload.u0, workload.p0)
 

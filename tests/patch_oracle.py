@@ -13,9 +13,11 @@ import numpy as np
 from oracle import lbm_oracle as O
 
 
-def one_step_at(params: O.Params, f, g, phiu_prev, have_prev: bool, cells, R: int = 4):
+def one_step_at(params: O.Params, f, g, phiu_prev, have_prev: bool, cells, R: int = 4,
+                t: int = 1):
     """FP64 populations (f[7], g[15]) after one oracle step at each (z, y, x) in cells,
-    starting from the given full state (arrays [q, z, y, x])."""
+    starting from the given full state (arrays [q, z, y, x]) at step count t (which only
+    matters for a time-dependent prescribed velocity)."""
     nz, ny, nx = f.shape[1:]
     if nx < 2 * R + 1 or ny < 2 * R + 1 or (not params.walls_z and nz < 2 * R + 1):
         raise ValueError("grid too small for the patch method")
@@ -31,11 +33,12 @@ def one_step_at(params: O.Params, f, g, phiu_prev, have_prev: bool, cells, R: in
             zc = R
         ix = np.ix_(zs, ys, xs)
         p = replace(params, nx=len(xs), ny=len(ys), nz=len(zs))
-        o = O.Oracle(p)
+        o = O.Oracle(p, box=(nz, ny, nx), coords=(zs[:, None, None], ys[None, :, None],
+                                                  xs[None, None, :]))
         o.f = np.stack([a[ix] for a in f]).astype(np.float64)
         o.g = np.stack([a[ix] for a in g]).astype(np.float64)
         o.phiu_prev = np.stack([a[ix] for a in phiu_prev]).astype(np.float64) if have_prev else None
-        o.t = 1
+        o.t = t
         o.step(1)
         out_f.append(o.f[:, zc, R, R])
         out_g.append(o.g[:, zc, R, R])

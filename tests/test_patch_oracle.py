@@ -28,3 +28,18 @@ def test_patch_step_equals_full_step(walls):
     for k, (z, y, x) in enumerate(cells):
         np.testing.assert_allclose(pf[k], o.f[:, z, y, x], atol=1e-14)
         np.testing.assert_allclose(pg[k], o.g[:, z, y, x], atol=1e-14)
+
+
+def test_patch_step_equals_full_step_in_tracking_mode():
+    """The prescribed velocity is evaluated at the patch's global coordinates and time."""
+    w = I.deformation(n=14, period=40.0)
+    p = O.Params.from_workload(w)
+    o = O.Oracle(p)
+    o.init(w.phi0)
+    o.step(7)
+    f, g, phiu = o.f.copy(), o.g.copy(), o.phiu_prev.copy()
+    cells = sample_cells(w.shape, 10, seed=2)
+    pf, _ = one_step_at(p, f, g, phiu, True, cells, R=4, t=o.t)
+    o.step(1)
+    for k, (z, y, x) in enumerate(cells):
+        np.testing.assert_allclose(pf[k], o.f[:, z, y, x], atol=1e-14)
