@@ -55,7 +55,13 @@ typedef struct {
 } lbm_grid;
 
 /* Flags for lbm_params.flags. */
-#define LBM_FLAG_BUOYANCY 1u /* G = (rho - (rho_l + rho_g)/2) g instead of G = rho g */
+#define LBM_FLAG_BUOYANCY 1u     /* G = (rho - (rho_l + rho_g)/2) g instead of G = rho g  */
+#define LBM_FLAG_SRT_FLOW 2u     /* single-relaxation-time flow lattice: every lambda_k
+                                    is the viscous rate 1/(nu(phi)/c_s^2 + 1/2), the SRT
+                                    special case named after Eq. 10                     */
+#define LBM_FLAG_D3Q7_STENCIL 4u /* Eqs. 35-36 with the D3Q7 lattice's weights: 7-point
+                                    central differences instead of the 15-point D3Q15
+                                    stencil                                             */
 
 /* Storage types for lbm_params.storage. */
 #define LBM_STORAGE_FP32 0
@@ -83,7 +89,7 @@ typedef struct {
   double sf[7];        /* S^f = diag(s_0..s_6), 0 < s_i < 2, s_1 = s_2 = s_3 (Eq. 10)*/
   double sg[15];       /* S^g = diag(lambda_0..lambda_14), 0 < lambda < 2 (Eq. 26);
                           lambda_9..13 are ignored: they follow nu(phi)              */
-  unsigned flags;      /* LBM_FLAG_*                                                  */
+  unsigned flags;      /* LBM_FLAG_*; any other bit is LBM_EINVAL                     */
   int storage;         /* LBM_STORAGE_FP32                                            */
   int pattern;         /* LBM_PATTERN_AB (default, 0) or LBM_PATTERN_AA               */
 } lbm_params;

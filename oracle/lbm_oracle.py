@@ -252,23 +252,35 @@ def neighbour(chi: np.ndarray, c: Sequence[int], walls_z: bool) -> np.ndarray:
     return np.take(out, idx, axis=-3)
 
 
-def grad_iso(chi: np.ndarray, walls_z: bool) -> np.ndarray:
+def _stencil_lattice(lattice: str):
+    """(velocities, weights, c_s^2) of the lattice whose weights the schemes use: the
+    D3Q15 flow lattice (default), or the D3Q7 lattice (weights A/2 with c_s^2 = A; the
+    schemes then reduce to 7-point central differences for any A)."""
+    if lattice == "d3q15":
+        return D3Q15_C, D3Q15_W, D3Q15_CS2
+    A = 0.25
+    return D3Q7_C, d3q7_weights(A), A
+
+
+def grad_iso(chi: np.ndarray, walls_z: bool, lattice: str = "d3q15") -> np.ndarray:
     """Eq. 35: grad chi = sum_{i != 0} omega_i c_i chi(x + c_i) / c_s^2."""
+    C, W, cs2 = _stencil_lattice(lattice)
     out = np.zeros((3,) + chi.shape)
-    for i in range(1, 15):
-        nb = neighbour(chi, D3Q15_C[i], walls_z)
+    for i in range(1, len(C)):
+        nb = neighbour(chi, C[i], walls_z)
         for a in range(3):
-            if D3Q15_C[i, a]:
-                out[a] += D3Q15_W[i] * D3Q15_C[i, a] * nb
-    return out / D3Q15_CS2
+            if C[i, a]:
+                out[a] += W[i] * C[i, a] * nb
+    return out / cs2
 
 
-def lap_iso(chi: np.ndarray, walls_z: bool) -> np.ndarray:
+def lap_iso(chi: np.ndarray, walls_z: bool, lattice: str = "d3q15") -> np.ndarray:
     """Eq. 36: lap chi = sum_{i != 0} 2 omega_i [chi(x + c_i) - chi(x)] / c_s^2."""
+    C, W, cs2 = _stencil_lattice(lattice)
     out = np.zeros_like(chi)
-    for i in range(1, 15):
-        out += 2.0 * D3Q15_W[i] * (neighbour(chi, D3Q15_C[i], walls_z) - chi)
-    return out / D3Q15_CS2
+    for i in range(1, len(C)):
+        out += 2.0 * W[i] * (neighbour(chi, C[i], walls_z) - chi)
+    return out / cs2
 
 
 # ----------------------------------------------------------------------------------
@@ -403,6 +415,10 @@ class Params:
     # interface tracking with a prescribed velocity instead of the flow lattice:
     # None (coupled), ("rotation", U) or ("deformation", U, period_in_steps)
     velocity: Optional[tuple] = None
+    # the paper's comparison variants: single-relaxation-time flow lattice (every
+    # lambda_k = the viscous rate), and the D3Q7 weights in the schemes of Eqs. 35-36
+    srt_flow: bool = False
+    stencil: str = "d3q15"
 
     @property
     def kappa(self):
@@ -429,7 +445,9 @@ class Params:
         return cls(nx=w.nx, ny=w.ny, nz=w.nz, walls_z=bool(w.walls_z), rho_l=w.rho_l,
                    rho_g=w.rho_g, nu_l=w.nu_l, nu_g=w.nu_g, mobility=w.mobility, D=w.D,
                    sigma=w.sigma, g=tuple(w.g), A=w.A, sf=tuple(w.sf), sg=tuple(w.sg),
-                   buoyancy=bool(w.buoyancy), velocity=getattr(w, "velocity", None))
+                   buoyancy=bool(w.buoyancy), velocity=getattr(w, "velocity", None),
+                   srt_flow=bool(getattr(w, "srt_flow", False)),
+                   stencil=getattr(w, "stencil", "d3q15"))
 
 
 class Oracle:
@@ -470,15 +488,15 @@ class Oracle:
     def macroscopic(self):
         """All macroscopic fields at the current time from the current populations."""
         p = self.p
-        wz = p.walls_z
+        wz, lat = p.walls_z, p.stencil
         phi = order_parameter(self.f)
         rho = density(phi, p.rho_l, p.rho_g)
-        mu = chemical_potential(phi, lap_iso(phi, wz), p.beta, p.kappa)
+        mu = chemical_potential(phi, lap_iso(phi, wz, lat), p.beta, p.kappa)
         if p.velocity is not None:
             return dict(phi=phi, rho=rho, mu=mu, u=self._prescribed(), p=np.zeros_like(phi))
-        grad_phi = grad_iso(phi, wz)
-        grad_rho = grad_iso(rho, wz)
-        lap_mu = lap_iso(mu, wz)
+        grad_phi = grad_iso(phi, wz, lat)
+        grad_rho = grad_iso(rho, wz, lat)
+        lap_mu = lap_iso(mu, wz, lat)
         Fs = mu[None] * grad_phi
         G = self._force(rho)
         u = velocity(self.g, rho, Fs, G, lap_mu, p.rho_l, p.rho_g, p.mobility)
@@ -495,7 +513,7 @@ class Oracle:
         phi0 = np.asarray(phi0, dtype=np.float64).reshape(shape)
         u0 = np.zeros((3,) + shape) if u0 is None else np.asarray(u0, np.float64).reshape((3,) + shape)
         p0 = np.zeros(shape) if p0 is None else np.asarray(p0, np.float64).reshape(shape)
-        mu0 = chemical_potential(phi0, lap_iso(phi0, p.walls_z), p.beta, p.kappa)
+        mu0 = chemical_potential(phi0, lap_iso(phi0, p.walls_z, p.stencil), p.beta, p.kappa)
         rho0 = density(phi0, p.rho_l, p.rho_g)
         self.t = 0
         if p.velocity is not None:
@@ -518,7 +536,10 @@ class Oracle:
         if p.velocity is None:
             rates_g = np.broadcast_to(np.asarray(p.sg, np.float64).reshape(15, 1, 1, 1),
                                       (15,) + phi.shape).copy()
-            rates_g[9:14] = p.viscous_rate(phi)[None]
+            if p.srt_flow:
+                rates_g[:] = p.viscous_rate(phi)[None]
+            else:
+                rates_g[9:14] = p.viscous_rate(phi)[None]
             mg = to_moments(GAMMA, self.g)
             mg_post = collide_moments(mg, d3q15_mgeq(mac["p"], rho, u), rates_g,
                                       d3q15_mT(u, mac["grad_rho"], mac["F"]))

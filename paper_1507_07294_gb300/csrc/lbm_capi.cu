@@ -110,6 +110,8 @@ lbm::Physics make_physics(const lbm_params& p) {
   ph.rho_ref = (p.flags & LBM_FLAG_BUOYANCY) ? static_cast<float>(0.5 * (p.rho_l + p.rho_g)) : 0.0f;
   for (int k = 0; k < 7; ++k) ph.sf[k] = static_cast<float>(p.sf[k]);
   for (int k = 0; k < 15; ++k) ph.sg[k] = static_cast<float>(p.sg[k]);
+  ph.srt_flow = (p.flags & LBM_FLAG_SRT_FLOW) ? 1 : 0;
+  ph.d3q7_stencil = (p.flags & LBM_FLAG_D3Q7_STENCIL) ? 1 : 0;
   return ph;
 }
 
@@ -135,6 +137,8 @@ lbm_status validate(const lbm_grid* g, const lbm_params* p) {
     return fail(nullptr, LBM_EINVAL, "Eq. 19 needs s_1 = s_2 = s_3");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->g[a])) return fail(nullptr, LBM_EINVAL, "g must be finite");
+  if (p->flags & ~(LBM_FLAG_BUOYANCY | LBM_FLAG_SRT_FLOW | LBM_FLAG_D3Q7_STENCIL))
+    return fail(nullptr, LBM_EINVAL, "unknown flag");
   if (p->storage != LBM_STORAGE_FP32) return fail(nullptr, LBM_EINVAL, "unknown storage type");
   if (p->pattern != LBM_PATTERN_AB && p->pattern != LBM_PATTERN_AA)
     return fail(nullptr, LBM_EINVAL, "unknown population pattern");

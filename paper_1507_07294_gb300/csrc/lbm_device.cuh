@@ -49,7 +49,13 @@ struct Physics {
   float sg[15];      // S^g (Eq. 26), entries 9..13 unused (viscous, per cell)
   int vel_kind;      // 0: coupled; else the prescribed velocity field (VelocityKind)
   float vel_U;       // its amplitude U
+  int srt_flow;      // 1: every D3Q15 rate is the viscous one (single relaxation time)
+  int d3q7_stencil;  // 1: Eqs. 35-36 with the D3Q7 weights (7-point central differences)
 };
+
+// Compile-time model variants of the step kernels (bit set): kVarSrtFlow, kVarD3Q7.
+constexpr int kVarSrtFlow = 1;
+constexpr int kVarD3Q7 = 2;
 
 // Prescribed velocity fields of the interface-tracking mode (Sec. III A, B).
 enum VelocityKind { kVelNone = 0, kVelUniform = 1, kVelRotation = 2, kVelDeformation = 3 };
@@ -287,6 +293,18 @@ __device__ __forceinline__ void load_stencil(const float* __restrict__ a, int id
   }
 }
 
+// The same schemes with the D3Q7 weights (omega_i / c_s^2 = 1/2 for every A): plain
+// central differences on the 6 faces.
+__device__ __forceinline__ float stencil_lap7(const Stencil& s) {
+  return ((s.xm + s.xp) + (s.ym + s.yp) + (s.zm + s.zp)) - 6.0f * s.c;
+}
+
+__device__ __forceinline__ void stencil_grad7(const Stencil& s, float g[3]) {
+  g[0] = 0.5f * (s.xp - s.xm);
+  g[1] = 0.5f * (s.yp - s.ym);
+  g[2] = 0.5f * (s.zp - s.zm);
+}
+
 __device__ __forceinline__ float stencil_lap(const Stencil& s) {
   const float faces = (s.xm + s.xp) + (s.ym + s.yp) + (s.zm + s.zp);
   const float corners = ((s.k[0] + s.k[1]) + (s.k[2] + s.k[3])) + ((s.k[4] + s.k[5]) + (s.k[6] + s.k[7]));
@@ -387,6 +405,7 @@ __device__ __forceinline__ Macro macroscopic(const Physics& ph, const float g[15
 // that the small correction is what passes through the FP32 back-transform.
 // Gamma^{-1} = Gamma^T diag(1/|row_k|^2), |row|^2 = 15,18,360,10,40,10,40,10,40,12,4,8,8,8,8.
 // ---------------------------------------------------------------------------------
+template <bool SRT = false>
 __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], const Macro& M,
                                               float lambda_visc) {
   // forward transform (rows as polynomials of c; see Eq. 25)
@@ -470,7 +489,7 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
   float a[15];
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
-    const float lam = (k >= 9 && k <= 13) ? lambda_visc : ph.sg[k];
+    const float lam = (SRT || (k >= 9 && k <= 13)) ? lambda_visc : ph.sg[k];
     a[k] = (lam * (m[k] - meq[k]) - (1.0f - 0.5f * lam) * mT[k]) * inv_n[k];
   }
 

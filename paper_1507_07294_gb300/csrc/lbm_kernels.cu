@@ -59,6 +59,7 @@ __device__ __forceinline__ int wrap(int v, int n, int span) {
   return v < 0 ? v + n : v;
 }
 
+template <bool D3Q7>
 __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
                                                  float* __restrict__ mu, Geometry geo,
                                                  Physics ph) {
@@ -96,9 +97,11 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
   for (int l = 1; l <= nl; ++l) {
     float c2, f2, d2;
     plane(l + 1, c2, f2, d2);
-    // Eq. 36 on the D3Q15 stencil: 2/3 (faces - 6 c) + 1/12 (corners - 8 c)
-    const float lap = (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
-                      (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
+    // Eq. 36 on the D3Q15 stencil: 2/3 (faces - 6 c) + 1/12 (corners - 8 c); with the
+    // D3Q7 weights: faces - 6 c
+    const float lap = D3Q7 ? (f1 + (c0 + c2)) - 6.0f * c1
+                           : (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
+                                 (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
     out[(l - 1) * zstride] = chemical_potential(ph, c1, lap);
     c0 = c1; f0 = f1; d0 = d1;
     c1 = c2; f1 = f2; d1 = d2;
@@ -110,6 +113,7 @@ struct CellStencils {
   float grad_phi[3], lap_mu, phi, mu;
 };
 
+template <bool D3Q7 = false>
 __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ phi,
                                                       const float* __restrict__ mu, int idx,
                                                       const Nbr& nb) {
@@ -117,13 +121,16 @@ __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ 
   {
     Stencil s;
     load_stencil(phi, idx, nb, s);
-    stencil_grad(s, cs.grad_phi);
+    if (D3Q7)
+      stencil_grad7(s, cs.grad_phi);
+    else
+      stencil_grad(s, cs.grad_phi);
     cs.phi = s.c;
   }
   {
     Stencil s;
     load_stencil(mu, idx, nb, s);
-    cs.lap_mu = stencil_lap(s);
+    cs.lap_mu = D3Q7 ? stencil_lap7(s) : stencil_lap(s);
     cs.mu = s.c;
   }
   return cs;
@@ -135,7 +142,7 @@ __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ 
 #ifndef LBM_COLLIDE_MIN_BLOCKS
 #define LBM_COLLIDE_MIN_BLOCKS 3
 #endif
-template <int P>
+template <int P, int VAR>
 __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
     k_collide(const float* src, float* dst, const float* __restrict__ phi,
               const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev) {
@@ -152,10 +159,10 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
 #pragma unroll
   for (int a = 0; a < 3; ++a) prev[a] = src[own + a * kTile];
 
-  const CellStencils cs = cell_stencils(phi, mu, idx, nb);
+  const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
-  collide_d3q15(ph, g, M, lambda_visc);
+  collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
   store_g<P>(dst, idx, nb, g);
 
   // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
@@ -228,7 +235,8 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src
     return;
   }
   const Nbr nb = make_nbr(geo, x, y, z);
-  const CellStencils cs = cell_stencils(phi, mu, idx, nb);
+  const CellStencils cs = ph.d3q7_stencil ? cell_stencils<true>(phi, mu, idx, nb)
+                                          : cell_stencils<false>(phi, mu, idx, nb);
   float g[15];
   load_g<P>(src, idx, nb, g);
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
@@ -450,14 +458,38 @@ cudaError_t launch_phi(const float* src, float* phi, const Geometry& geo, int pa
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st) {
   const dim3 grid((geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY, (geo.nz + kTZ - 1) / kTZ);
-  k_mu<<<grid, dim3(kTX, kTY), 0, st>>>(phi, mu, geo, ph);
+  if (ph.d3q7_stencil)
+    k_mu<true><<<grid, dim3(kTX, kTY), 0, st>>>(phi, mu, geo, ph);
+  else
+    k_mu<false><<<grid, dim3(kTX, kTY), 0, st>>>(phi, mu, geo, ph);
   return cudaGetLastError();
+}
+
+template <int VAR>
+void collide_variant(const float* src, float* dst, const float* phi, const float* mu,
+                     const Geometry& geo, const Physics& ph, int pattern, int prev,
+                     cudaStream_t st) {
+  const unsigned blocks = blocks_for(geo.n);
+  if (pattern == kAB)
+    k_collide<kAB, VAR><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+  else if (pattern == kAAEven)
+    k_collide<kAAEven, VAR><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+  else
+    k_collide<kAAOdd, VAR><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
 }
 
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
                            const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                            cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_collide, src, dst, phi, mu, geo, ph, have_prev ? 1 : 0);
+  const int prev = have_prev ? 1 : 0;
+  const int var = (ph.srt_flow ? kVarSrtFlow : 0) | (ph.d3q7_stencil ? kVarD3Q7 : 0);
+  switch (var) {
+    case 0: collide_variant<0>(src, dst, phi, mu, geo, ph, pattern, prev, st); break;
+    case kVarSrtFlow: collide_variant<kVarSrtFlow>(src, dst, phi, mu, geo, ph, pattern, prev, st); break;
+    case kVarD3Q7: collide_variant<kVarD3Q7>(src, dst, phi, mu, geo, ph, pattern, prev, st); break;
+    default:
+      collide_variant<kVarSrtFlow | kVarD3Q7>(src, dst, phi, mu, geo, ph, pattern, prev, st);
+  }
   return cudaGetLastError();
 }
 

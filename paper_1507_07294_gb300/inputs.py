@@ -58,6 +58,9 @@ class Workload:
     # interface tracking with a prescribed velocity (no flow lattice):
     # None, ("uniform", U), ("rotation", U) or ("deformation", U, period_in_steps)
     velocity: Optional[tuple] = None
+    # the paper's comparison variants (Sec. III A): SRT flow lattice; D3Q7 stencils
+    srt_flow: bool = False
+    stencil: str = "d3q15"
     phi0: Optional[np.ndarray] = field(default=None, repr=False)
     u0: Optional[np.ndarray] = field(default=None, repr=False)
     p0: Optional[np.ndarray] = field(default=None, repr=False)

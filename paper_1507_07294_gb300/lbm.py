@@ -24,7 +24,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EBUS
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_EUNSTABLE", 5: "LBM_ETIMEOUT", 6: "LBM_EBUSY"}
 
-LBM_FLAG_BUOYANCY = 1
+LBM_FLAG_BUOYANCY, LBM_FLAG_SRT_FLOW, LBM_FLAG_D3Q7_STENCIL = 1, 2, 4
 LBM_STORAGE_FP32 = 0
 LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
 PATTERNS = {"ab": LBM_PATTERN_AB, "aa": LBM_PATTERN_AA}
@@ -121,14 +121,16 @@ def _ptr(a: Optional[np.ndarray]):
 
 def make_params(rho_l, rho_g, nu_l, nu_g, mobility, D, sigma, g=(0.0, 0.0, 0.0), A=0.25,
                 sf=(1.0, 1.25, 1.25, 1.25, 1.2, 1.0, 1.0), sg=(1.0,) * 15, buoyancy=False,
-                storage=LBM_STORAGE_FP32, pattern=LBM_PATTERN_AB) -> LbmParams:
+                storage=LBM_STORAGE_FP32, pattern=LBM_PATTERN_AB, srt_flow=False,
+                stencil="d3q15") -> LbmParams:
     p = LbmParams()
     p.rho_l, p.rho_g, p.nu_l, p.nu_g = rho_l, rho_g, nu_l, nu_g
     p.mobility, p.D, p.sigma, p.A = mobility, D, sigma, A
     p.g[:] = [float(v) for v in g]
     p.sf[:] = [float(v) for v in sf]
     p.sg[:] = [float(v) for v in sg]
-    p.flags = LBM_FLAG_BUOYANCY if buoyancy else 0
+    p.flags = ((LBM_FLAG_BUOYANCY if buoyancy else 0) | (LBM_FLAG_SRT_FLOW if srt_flow else 0)
+               | (LBM_FLAG_D3Q7_STENCIL if stencil == "d3q7" else 0))
     p.storage = storage
     p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
     return p
@@ -137,7 +139,9 @@ def make_params(rho_l, rho_g, nu_l, nu_g, mobility, D, sigma, g=(0.0, 0.0, 0.0),
 def params_from_workload(w, pattern=LBM_PATTERN_AB) -> tuple:
     grid = LbmGrid(w.nx, w.ny, w.nz, 1 if w.walls_z else 0)
     params = make_params(w.rho_l, w.rho_g, w.nu_l, w.nu_g, w.mobility, w.D, w.sigma, w.g, w.A,
-                         w.sf, w.sg, w.buoyancy, pattern=pattern)
+                         w.sf, w.sg, w.buoyancy, pattern=pattern,
+                         srt_flow=getattr(w, "srt_flow", False),
+                         stencil=getattr(w, "stencil", "d3q15"))
     return grid, params
 
 

@@ -65,6 +65,7 @@ def _good():
     (lambda g, p: p.sg.__setitem__(0, 0.0), "sg rates"),
     (lambda g, p: setattr(p, "storage", 7), "storage"),
     (lambda g, p: setattr(p, "pattern", 2), "pattern"),
+    (lambda g, p: setattr(p, "flags", 8), "flag"),
     (lambda g, p: (setattr(g, "nx", 2048), setattr(g, "ny", 1024), setattr(g, "nz", 1024)), "2^31"),
 ])
 def test_create_rejects_bad_arguments(lib, mutate, expect):

@@ -270,3 +270,18 @@ def test_patterns_agree_bit_for_bit(L):
             sa, sb = a.state(), b.state()
             for x, y in zip(sa[:3], sb[:3]):
                 assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("variant", ["srt_flow", "d3q7_stencil", "both"])
+def test_comparison_variants_100_steps(L, variant):
+    """The paper's comparison variants as flags: SRT flow lattice, D3Q7-weighted
+    difference schemes; walls and gravity on, 100 steps."""
+    w = I.perturbed(I.rayleigh_taylor(W=20, nz=40, Re=150.0), seed=17, u_amp=0.01, p_amp=1e-4)
+    w.srt_flow = variant in ("srt_flow", "both")
+    w.stencil = "d3q7" if variant in ("d3q7_stencil", "both") else "d3q15"
+    with L.Solver(w) as s:
+        s.step(100)
+        gf = s.fields()
+    o = _oracle(w)
+    o.step(100)
+    _compare_fields(gf, o.fields(), w.U, p_tol=1e-6)

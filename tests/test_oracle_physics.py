@@ -187,3 +187,36 @@ def test_time_derivative_is_the_backward_difference(monkeypatch):
     expected = fl1["phi"][None] * fl1["u"] - fl0["phi"][None] * fl0["u"]
     np.testing.assert_allclose(seen[1], expected, atol=1e-16)
     assert np.abs(expected).max() > 1e-5
+
+
+def test_srt_flow_with_unit_rates_equals_mrt_with_unit_rates():
+    """The SRT flow lattice sets every lambda_k to the viscous rate; with nu = 1/6 that
+    rate is 1, the same as an MRT run whose rates are all 1."""
+    w = I.perturbed(I.droplet(n=10, R=3.0, nu=1.0 / 6.0), seed=15, u_amp=0.01, p_amp=1e-3)
+    a = _oracle(w)
+    a.step(5)
+    w.srt_flow = True
+    b = _oracle(w)
+    b.step(5)
+    np.testing.assert_allclose(a.g, b.g, atol=1e-16)
+    np.testing.assert_allclose(a.f, b.f, atol=1e-16)
+
+
+def test_srt_flow_relaxes_all_moments_at_the_viscous_rate(monkeypatch):
+    """With srt_flow every D3Q15 moment relaxes at 1/(nu/c_s^2 + 1/2) (text after Eq. 10
+    for the SRT special case, Eq. 33 for the rate)."""
+    w = I.perturbed(I.droplet(n=8, R=2.5, nu=0.05), seed=16, u_amp=0.01, p_amp=1e-3)
+    w.srt_flow = True
+    o = _oracle(w)
+    seen = []
+    orig = O.collide_moments
+
+    def spy(m, meq, rates, msrc):
+        seen.append(np.array(rates, copy=True))
+        return orig(m, meq, rates, msrc)
+
+    monkeypatch.setattr(O, "collide_moments", spy)
+    o.step(1)
+    rates_g = seen[0]
+    assert rates_g.shape[0] == 15
+    np.testing.assert_allclose(rates_g, 1.0 / (3 * 0.05 + 0.5))

@@ -132,3 +132,16 @@ def test_stream_is_a_permutation(walls):
     post = rng.uniform(size=(15, 6, 5, 4))
     out = O.stream(post, O.D3Q15_C, O.OPP15, walls)
     np.testing.assert_array_equal(np.sort(out.ravel()), np.sort(post.ravel()))
+
+
+@pytest.mark.parametrize("m", [(1, 0, 0), (1, 2, 3), (3, 4, 5)])
+def test_d3q7_weighted_schemes_are_central_differences(m):
+    """With the D3Q7 weights (omega_i / c_s^2 = 1/2) Eqs. 35-36 become the 7-point
+    central differences: lap symbol 2 sum_a (cos k_a - 1), grad symbol sin k_a."""
+    shape = (12, 10, 8)
+    k, arg = _plane_wave(shape, m)
+    L7 = 2 * np.sum(np.cos(k) - 1)
+    np.testing.assert_allclose(O.lap_iso(np.cos(arg), False, "d3q7"), L7 * np.cos(arg), atol=1e-13)
+    got = O.grad_iso(np.cos(arg), False, "d3q7")
+    for a in range(3):
+        np.testing.assert_allclose(got[a], -np.sin(k[a]) * np.sin(arg), atol=1e-13)
