@@ -177,6 +177,17 @@ lbm_status lbm_read_state(lbm_ctx* ctx, float* f, float* g, float* phiu_prev,
 lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
                            const float* phiu_prev, long long step);
 
+/* Tuning parameters (no effect on results, only on speed).
+ * LBM_TUNE_PREFETCH_COLLIDE / LBM_TUNE_PREFETCH_PHI: how many thread blocks ahead the
+ * fused stream-collide kernel / the order-parameter kernel prefetch cell data into L2
+ * (0 disables).  Default: one wave, the number of SMs times the kernel's resident
+ * blocks per SM, set by lbm_create.  lbm_set_tuning returns LBM_EINVAL for an unknown
+ * parameter or a negative value. */
+#define LBM_TUNE_PREFETCH_COLLIDE 0
+#define LBM_TUNE_PREFETCH_PHI 1
+lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
+lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
+
 /* Number of steps taken since lbm_init_phi / lbm_write_state. */
 lbm_status lbm_get_step(const lbm_ctx* ctx, long long* step);
 

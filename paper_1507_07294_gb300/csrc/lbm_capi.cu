@@ -235,6 +235,15 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   c->geo.stride = static_cast<size_t>((n + 63) / 64 * 64);  // 256-byte aligned planes
   c->geo.div_nx = make_fast_div(static_cast<unsigned>(grid->nx));
   c->geo.div_ny = make_fast_div(static_cast<unsigned>(grid->ny));
+  // L2 prefetch distances: one wave of resident blocks
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      c->geo.prefetch_collide = sms * lbm::resident_blocks_per_sm(0);
+      c->geo.prefetch_phi = sms * lbm::resident_blocks_per_sm(1);
+    }
+  }
   c->ph = make_physics(*params);
 
   const size_t plane = c->geo.stride * sizeof(float);
@@ -438,6 +447,25 @@ lbm_status lbm_set_velocity(lbm_ctx* c, int kind, double U, double period) {
   c->ph.vel_kind = kind;
   c->ph.vel_U = static_cast<float>(U);
   return LBM_OK;
+}
+
+lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
+  if (!c) return LBM_EINVAL;
+  if (value < 0) return fail(c, LBM_EINVAL, "tuning values must be >= 0");
+  switch (param) {
+    case LBM_TUNE_PREFETCH_COLLIDE: c->geo.prefetch_collide = value; return LBM_OK;
+    case LBM_TUNE_PREFETCH_PHI: c->geo.prefetch_phi = value; return LBM_OK;
+    default: return fail(c, LBM_EINVAL, "unknown tuning parameter");
+  }
+}
+
+lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
+  if (!c || !value) return LBM_EINVAL;
+  switch (param) {
+    case LBM_TUNE_PREFETCH_COLLIDE: *value = c->geo.prefetch_collide; return LBM_OK;
+    case LBM_TUNE_PREFETCH_PHI: *value = c->geo.prefetch_phi; return LBM_OK;
+    default: return LBM_EINVAL;
+  }
 }
 
 lbm_status lbm_get_step(const lbm_ctx* c, long long* step) {

@@ -28,6 +28,8 @@ struct Geometry {
   int plane;       // nx * ny
   size_t stride;   // elements between consecutive planes of dense per-cell arrays
   FastDiv div_nx, div_ny;
+  int prefetch_collide;  // L2 prefetch distance of k_collide in blocks (0: none)
+  int prefetch_phi;      // same for k_phi
 };
 
 __device__ __forceinline__ int fast_div(int n, const FastDiv& f) {

@@ -37,6 +37,8 @@ cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo
                            int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
+// Resident blocks per SM of k_collide (kernel 0) or k_phi (kernel 1); 0 on error.
+int resident_blocks_per_sm(int kernel);
 cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
                           const Geometry& geo, int pattern, bool with_g, cudaStream_t st);
 // Floats of the tiled cell-state array for n cells.
@@ -47,6 +49,8 @@ cudaError_t launch_gather(const float* pop, float* dense, const Geometry& geo, b
                           int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
+// Resident blocks per SM of k_collide (kernel 0) or k_phi (kernel 1); 0 on error.
+int resident_blocks_per_sm(int kernel);
 cudaError_t launch_reduce(const float* pop, const float* phi, double* partial, double* out,
                           const Geometry& geo, bool odd, cudaStream_t st);
 

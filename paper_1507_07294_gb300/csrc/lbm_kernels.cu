@@ -27,10 +27,45 @@ __device__ __forceinline__ void cell_coords(const Geometry& geo, int idx, int& x
   y = r - z * geo.ny;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (a hint: no completion to wait for).  p must be
+// 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Latency hiding for the streaming kernels: thread 0 of block b prefetches into L2 the
+// data of the cells of block b + dist, which a block of the next wave will stream in
+// (dist = one wave: SMs x resident blocks per SM).  k_collide prefetches the whole cell
+// state of those cells (all 25 slots) and their phi and mu; k_phi only the 7 f slots of
+// each tile.  All ranges are clipped to the arrays.
+template <bool ALL_SLOTS>
+__device__ __forceinline__ void prefetch_ahead(const float* state, const float* phi, const float* mu,
+                                               const Geometry& geo, int dist) {
+  if (dist <= 0 || threadIdx.x != 0) return;
+  const long long first = static_cast<long long>(blockIdx.x + dist) * kBlock;
+  if (first >= geo.n) return;
+  const long long cells = min(static_cast<long long>(kBlock), geo.n - first);
+  // kBlock is a multiple of kTile, so `first` starts a tile
+  const int tiles = static_cast<int>((cells + kTile - 1) / kTile);
+  const float* t0 = state + tile_base(static_cast<int>(first));
+  if (ALL_SLOTS) {
+    prefetch_l2(t0, static_cast<unsigned>(tiles * kTileSlots * kTile * sizeof(float)));
+    const unsigned bytes = static_cast<unsigned>(cells * sizeof(float)) & ~15u;
+    if (bytes) {
+      prefetch_l2(phi + first, bytes);
+      prefetch_l2(mu + first, bytes);
+    }
+  } else {
+    for (int t = 0; t < tiles; ++t)
+      prefetch_l2(t0 + t * (kTileSlots * kTile), kQ7 * kTile * sizeof(float));
+  }
+}
+
 // ------------------------------------------------------------------ k_phi ---------
 template <int P>
 __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
                                                 float* __restrict__ phi, Geometry geo) {
+  prefetch_ahead<false>(src, nullptr, nullptr, geo, geo.prefetch_phi);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
   int x, y, z;
@@ -142,10 +177,12 @@ __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ 
 #ifndef LBM_COLLIDE_MIN_BLOCKS
 #define LBM_COLLIDE_MIN_BLOCKS 3
 #endif
+
 template <int P, int VAR>
 __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
     k_collide(const float* src, float* dst, const float* __restrict__ phi,
               const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev) {
+  prefetch_ahead<true>(src, phi, mu, geo, geo.prefetch_collide);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
   int x, y, z;
@@ -529,6 +566,14 @@ cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st) {
   k_convert<<<blocks_for(n), kBlock, 0, st>>>(in, out, n);
   return cudaGetLastError();
+}
+
+int resident_blocks_per_sm(int kernel) {
+  int blocks = 0;
+  cudaError_t e = kernel == 0
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0>, kBlock, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi<kAB>, kBlock, 0);
+  return e == cudaSuccess ? blocks : 0;
 }
 
 int reduce_parts(const Geometry& geo) {

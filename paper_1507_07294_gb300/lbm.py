@@ -36,6 +36,8 @@ LBM_VELOCITY_NONE, LBM_VELOCITY_UNIFORM, LBM_VELOCITY_ROTATION, LBM_VELOCITY_DEF
 VELOCITY_KINDS = {"uniform": LBM_VELOCITY_UNIFORM, "rotation": LBM_VELOCITY_ROTATION,
                   "deformation": LBM_VELOCITY_DEFORMATION}
 
+LBM_TUNE_PREFETCH_COLLIDE, LBM_TUNE_PREFETCH_PHI = 0, 1
+
 KERNEL_PHI, KERNEL_MU, KERNEL_COLLIDE = 0, 1, 2
 KERNEL_NAMES = ("k_phi", "k_mu", "k_collide")
 
@@ -79,6 +81,8 @@ _SIGNATURES = {
     "lbm_write_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_longlong]),
     "lbm_get_step": (c_int, [c_void_p, POINTER(c_longlong)]),
     "lbm_set_velocity": (c_int, [c_void_p, c_int, c_double, c_double]),
+    "lbm_set_tuning": (c_int, [c_void_p, c_int, c_int]),
+    "lbm_get_tuning": (c_int, [c_void_p, c_int, POINTER(c_int)]),
     "lbm_profile": (c_int, [c_void_p, c_int]),
     "lbm_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_longlong)]),
     "lbm_field_sum_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_void_p]),
@@ -279,6 +283,18 @@ def lbm_set_velocity(ctx: Context, kind, U: float = 0.0, period: float = 1.0) ->
     lib = load_library()
     k = VELOCITY_KINDS[kind] if isinstance(kind, str) else int(kind)
     _check(lib, lib.lbm_set_velocity(ctx.handle, k, float(U), float(period)), ctx.handle)
+
+
+def lbm_set_tuning(ctx: Context, param: int, value: int) -> None:
+    lib = load_library()
+    _check(lib, lib.lbm_set_tuning(ctx.handle, int(param), int(value)), ctx.handle)
+
+
+def lbm_get_tuning(ctx: Context, param: int) -> int:
+    lib = load_library()
+    v = c_int()
+    _check(lib, lib.lbm_get_tuning(ctx.handle, int(param), ctypes.byref(v)), ctx.handle)
+    return v.value
 
 
 def lbm_get_step(ctx: Context) -> int:
