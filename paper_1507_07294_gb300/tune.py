@@ -1,0 +1,49 @@
+"""Autotuning of launch parameters on a live run.
+
+The tuned parameters change only speed, never results: the L2 prefetch distances of
+the stream-collide and order-parameter kernels (lbm_set_tuning).  Each candidate is
+timed with the library's CUDA-event kernel profile over a few steps of the run itself,
+so tuning advances the simulation by (number of candidates) x (warm + steps) steps.
+"""
+from __future__ import annotations
+
+from typing import Dict, Iterable, Optional
+
+from . import lbm as L
+
+# candidate distances as fractions of the default (one wave of resident blocks)
+DEFAULT_FRACTIONS = (0.0, 0.67, 0.83, 1.0, 1.17)
+
+
+def _time_kernel(ctx, kernel: int, steps: int, warm: int) -> float:
+    L.lbm_step(ctx, warm)
+    L.lbm_profile(ctx, True)
+    L.lbm_step(ctx, steps)
+    ms, n = L.lbm_profile_read(ctx, kernel)
+    L.lbm_profile(ctx, False)
+    return ms / max(n, 1)
+
+
+def autotune(ctx, steps: int = 8, warm: int = 2,
+             fractions: Iterable[float] = DEFAULT_FRACTIONS) -> Dict[str, dict]:
+    """Pick the fastest prefetch distance for k_collide and k_phi; returns, per
+    parameter, the chosen value and the mean kernel time of every candidate (ms)."""
+    out = {}
+    for name, param, kernel in (("prefetch_collide", L.LBM_TUNE_PREFETCH_COLLIDE, L.KERNEL_COLLIDE),
+                                ("prefetch_phi", L.LBM_TUNE_PREFETCH_PHI, L.KERNEL_PHI)):
+        base = L.lbm_get_tuning(ctx, param)
+        cands = sorted({int(round(f * base)) for f in fractions})
+        times = {}
+        for v in cands:
+            L.lbm_set_tuning(ctx, param, v)
+            times[v] = _time_kernel(ctx, kernel, steps, warm)
+        best = min(times, key=times.get)
+        L.lbm_set_tuning(ctx, param, best)
+        out[name] = {"value": best, "default": base, "ms": {str(k): round(t, 5) for k, t in times.items()}}
+    return out
+
+
+def tuning_steps(steps: int = 8, warm: int = 2, fractions: Optional[Iterable[float]] = None) -> int:
+    """Number of time steps autotune() advances the run by."""
+    n = len(set(fractions or DEFAULT_FRACTIONS))
+    return 2 * n * (steps + warm)

@@ -285,3 +285,22 @@ def test_comparison_variants_100_steps(L, variant):
     o = _oracle(w)
     o.step(100)
     _compare_fields(gf, o.fields(), w.U, p_tol=1e-6)
+
+
+def test_autotune_changes_speed_not_results(L):
+    """Autotuning sets only prefetch distances: a tuned run and an untuned run advanced
+    by the same number of steps hold identical states."""
+    from paper_1507_07294_gb300 import tune
+    w = I.perturbed(I.rayleigh_taylor(W=32, nz=64, Re=200.0), seed=18, u_amp=0.01)
+    with L.Solver(w) as a:
+        chosen = tune.autotune(a.ctx, steps=2, warm=1)
+        n = a.t
+        sa = a.state()
+    assert n == tune.tuning_steps(steps=2, warm=1)
+    for name, d in chosen.items():
+        assert d["value"] in [int(k) for k in d["ms"]]
+    with L.Solver(w) as b:
+        b.step(n)
+        sb = b.state()
+    for x, y in zip(sa[:3], sb[:3]):
+        assert np.array_equal(x, y)
