@@ -45,6 +45,11 @@ UNIT = "MLUPS"
 COLLIDE_BYTES_PER_CELL = (22 + 3 + 2) * 4 + (22 + 3) * 4
 STEP_BYTES_PER_CELL = COLLIDE_BYTES_PER_CELL + (7 + 1) * 4 + (1 + 1) * 4  # + k_phi + k_mu
 
+# The same with 16-bit populations: 22 x 2 B populations + 12 B phi u, read and written,
+# plus phi and mu (k_collide); 7 x 2 B of f, the previous phi and the new phi (k_phi).
+COLLIDE_BYTES_PER_CELL_16 = 2 * (22 * 2 + 12) + 8
+STEP_BYTES_PER_CELL_16 = COLLIDE_BYTES_PER_CELL_16 + (7 * 2 + 4 + 4) + 8
+
 # DRAM traffic of k_collide per cell from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the cells of the captured launch), valid only for
 # the kernel source it was taken on (hash of csrc/lbm_device.cuh + lbm_kernels.cu).
@@ -299,10 +304,10 @@ def run_ours(args):
     max_over_ranks = group.max
 
     # ---- warm-up and autotuning (untimed) ------------------------------------
+    from paper_1507_07294_gb300 import tune
     solver.step(args.warmup)
     tuning = None
     if not args.no_tune:
-        from paper_1507_07294_gb300 import tune
         tuning = tune.autotune(ctx)
         torch.cuda.synchronize()
 
@@ -357,6 +362,37 @@ def run_ours(args):
                "d2h_bytes_per_step": round(5 * 8 + 5 * 4 * cells / args.steps),
                "seconds": round(t_e2e, 4)}
 
+    # ---- reduced-precision storage variants (same workload and step count) ------
+    variants = None
+    if not args.no_variants:
+        solver.close()
+        variants = {}
+        for storage in ("fp16", "bf16"):
+            vs = L.Solver(w, stream=stream.cuda_stream, storage=storage)
+            vs.step(args.warmup)
+            if not args.no_tune:
+                tune.autotune(vs.ctx)
+            L.lbm_profile(vs.ctx, True)
+            barrier()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            vs.step(args.steps)
+            v1.record(stream)
+            barrier()
+            vms = max_over_ranks(v0.elapsed_time(v1))
+            cms, cn = L.lbm_profile_read(vs.ctx, L.KERNEL_COLLIDE)
+            cmean = cms / max(cn, 1)
+            variants[storage] = {
+                "value": round(aggregate_mlups(cells, args.steps, world, vms * 1e-3), 3),
+                "unit": UNIT, "ms_per_step": round(vms / args.steps, 5),
+                "speedup_vs_fp32": round(elapsed_ms / vms, 3),
+                "k_collide_ms": round(cmean, 5),
+                "k_collide_bytes_per_cell": COLLIDE_BYTES_PER_CELL_16,
+                "k_collide_frac": round(COLLIDE_BYTES_PER_CELL_16 * cells / (cmean * 1e-3) / 1e9 / peak, 4),
+                "step_bytes_per_cell": STEP_BYTES_PER_CELL_16}
+            vs.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline()
@@ -378,11 +414,13 @@ def run_ours(args):
                                        (elapsed_ms * 1e-3) / 1e9 / peak, 4),
                 "kernels": kernels,
                 "tuning": {k: v["value"] for k, v in tuning.items()} if tuning else None,
+                "storage_variants": variants,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
                 "gpu_launches": 3 * args.steps,
                 "sum_phi": sum_phi}
         print(json.dumps(line), flush=True)
-    solver.close()
+    if variants is None:
+        solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -399,6 +437,8 @@ def main(argv=None):
                     help="population storage: two arrays (ab) or in place (aa)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the FP16/BF16 population-storage variants")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the untimed autotuning of prefetch distances")
     args = ap.parse_args(argv)

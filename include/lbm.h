@@ -63,8 +63,13 @@ typedef struct {
                                     central differences instead of the 15-point D3Q15
                                     stencil                                             */
 
-/* Storage types for lbm_params.storage. */
+/* Storage types of the populations for lbm_params.storage.  Arithmetic is FP32 in
+ * every case; phi u, phi and mu stay FP32.  With FP16/BF16 the population f_0 is kept as
+ * f_0 - phi (phi of the step that wrote it), since f_0 ~ phi ~ +-1 would lose ~3 decimal
+ * digits in 16 bits.  16-bit storage needs LBM_PATTERN_AB. */
 #define LBM_STORAGE_FP32 0
+#define LBM_STORAGE_FP16 1
+#define LBM_STORAGE_BF16 2
 
 /* Population storage patterns for lbm_params.pattern.
  * LBM_PATTERN_AB: two arrays; each step pulls from one and writes the other (176
@@ -90,7 +95,7 @@ typedef struct {
   double sg[15];       /* S^g = diag(lambda_0..lambda_14), 0 < lambda < 2 (Eq. 26);
                           lambda_9..13 are ignored: they follow nu(phi)              */
   unsigned flags;      /* LBM_FLAG_*; any other bit is LBM_EINVAL                     */
-  int storage;         /* LBM_STORAGE_FP32                                            */
+  int storage;         /* LBM_STORAGE_FP32 (default), LBM_STORAGE_FP16, LBM_STORAGE_BF16 */
   int pattern;         /* LBM_PATTERN_AB (default, 0) or LBM_PATTERN_AA               */
 } lbm_params;
 
@@ -114,9 +119,10 @@ typedef struct {
  * used); `cuda_stream` is a cudaStream_t or NULL.  Fails with LBM_EINVAL when a size
  * is < 1, N >= 2^31, a rate is outside (0, 2), s_1..3 differ, A is outside (0, 1/3),
  * a density or viscosity is not positive, or the storage type or pattern is unknown.
- * Device memory per cell (FP32): the cell state (22 populations + phi u of the
- * previous step, 100 bytes; twice for LBM_PATTERN_AB) + phi + mu + 5 staging floats,
- * i.e. 228 bytes (AB) or 128 bytes (AA). */
+ * Device memory per cell: the cell state (22 populations + phi u of the previous
+ * step: 100 bytes in FP32, 56 bytes with 16-bit populations; twice for LBM_PATTERN_AB)
+ * + phi + mu + 7 staging floats, i.e. 236 bytes (FP32, AB), 136 bytes (FP32, AA) or
+ * 148 bytes (16-bit, AB). */
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
                       const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out);
 

@@ -27,7 +27,8 @@ struct lbm_ctx {
   int cur = 0;             // array holding the current state (pattern AB)
   float* phi = nullptr;    // order parameter of the current step
   float* mu = nullptr;     // chemical potential of the current step
-  float* stage = nullptr;  // 5 planes: field read-out, state gather, init inputs
+  float* stage = nullptr;  // 7 planes: field read-out (rho, p, u, phi, mu), state
+                           // gather/scatter, initial u and p
   double* partial = nullptr;  // reduction partials
   double* red = nullptr;      // 5 reduction results
 
@@ -139,9 +140,13 @@ lbm_status validate(const lbm_grid* g, const lbm_params* p) {
     if (!std::isfinite(p->g[a])) return fail(nullptr, LBM_EINVAL, "g must be finite");
   if (p->flags & ~(LBM_FLAG_BUOYANCY | LBM_FLAG_SRT_FLOW | LBM_FLAG_D3Q7_STENCIL))
     return fail(nullptr, LBM_EINVAL, "unknown flag");
-  if (p->storage != LBM_STORAGE_FP32) return fail(nullptr, LBM_EINVAL, "unknown storage type");
+  if (p->storage != LBM_STORAGE_FP32 && p->storage != LBM_STORAGE_FP16 &&
+      p->storage != LBM_STORAGE_BF16)
+    return fail(nullptr, LBM_EINVAL, "unknown storage type");
   if (p->pattern != LBM_PATTERN_AB && p->pattern != LBM_PATTERN_AA)
     return fail(nullptr, LBM_EINVAL, "unknown population pattern");
+  if (p->storage != LBM_STORAGE_FP32 && p->pattern != LBM_PATTERN_AB)
+    return fail(nullptr, LBM_EINVAL, "16-bit storage needs LBM_PATTERN_AB");
   return LBM_OK;
 }
 
@@ -233,6 +238,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   c->geo.n = static_cast<int>(n);
   c->geo.plane = grid->nx * grid->ny;
   c->geo.stride = static_cast<size_t>((n + 63) / 64 * 64);  // 256-byte aligned planes
+  c->geo.storage = params->storage;  // LBM_STORAGE_* numbers match lbm::Storage
   c->geo.div_nx = make_fast_div(static_cast<unsigned>(grid->nx));
   c->geo.div_ny = make_fast_div(static_cast<unsigned>(grid->ny));
   // L2 prefetch distances: one wave of resident blocks
@@ -240,19 +246,19 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
-      c->geo.prefetch_collide = sms * lbm::resident_blocks_per_sm(0);
-      c->geo.prefetch_phi = sms * lbm::resident_blocks_per_sm(1);
+      c->geo.prefetch_collide = sms * lbm::resident_blocks_per_sm(0, c->geo.storage);
+      c->geo.prefetch_phi = sms * lbm::resident_blocks_per_sm(1, c->geo.storage);
     }
   }
   c->ph = make_physics(*params);
 
   const size_t plane = c->geo.stride * sizeof(float);
-  const size_t state_bytes = lbm::state_floats(c->geo.n) * sizeof(float);
+  const size_t state_bytes = lbm::state_bytes(c->geo.n, c->geo.storage);
   c->pop[0] = static_cast<float*>(dev_alloc(c, state_bytes));
   if (params->pattern == LBM_PATTERN_AB) c->pop[1] = static_cast<float*>(dev_alloc(c, state_bytes));
   c->phi = static_cast<float*>(dev_alloc(c, plane));
   c->mu = static_cast<float*>(dev_alloc(c, plane));
-  c->stage = static_cast<float*>(dev_alloc(c, plane * 5));
+  c->stage = static_cast<float*>(dev_alloc(c, plane * 7));
   c->partial = static_cast<double*>(dev_alloc(c, sizeof(double) * 5 * lbm::kReduceMaxParts));
   c->red = static_cast<double*>(dev_alloc(c, sizeof(double) * 8));
   if (!c->pop[0] || (params->pattern == LBM_PATTERN_AB && !c->pop[1]) || !c->phi || !c->mu ||
@@ -314,7 +320,7 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     const int pat = read_pattern(c);
     const float* src = cur_state(c);
     float* dst = c->params.pattern == LBM_PATTERN_AB ? c->pop[1 - c->cur] : c->pop[c->cur];
-    LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->geo, pat, c->stream); }));
+    LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->phi, c->geo, pat, c->stream); }));
     LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
     const bool prev = c->have_prev;
     if (c->vel_kind == LBM_VELOCITY_NONE) {
@@ -346,17 +352,21 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   if (((mask & LBM_FIELD_PHI) && !phi) || ((mask & LBM_FIELD_RHO) && !rho) ||
       ((mask & LBM_FIELD_P) && !p) || ((mask & LBM_FIELD_U) && !u) || ((mask & LBM_FIELD_MU) && !mu))
     return fail(c, LBM_EINVAL, "a selected field has a NULL buffer");
-  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, c->geo, read_pattern(c), c->stream));
-  LBM_CK(c, lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream));
-  if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
-    LBM_CK(c, lbm::launch_fields(cur_state(c), c->phi, c->mu, c->stage, c->geo, c->ph,
-                                 read_pattern(c), velocity_time_factor(c, c->step), c->stream));
+  // phi and mu of the current state into staging planes 5 and 6: the solver's own phi
+  // array is the reference of the 16-bit slot 0 and must keep the previous step's phi.
   const size_t n = static_cast<size_t>(c->geo.n);
   const size_t s = c->geo.stride;
+  float* phi_now = c->stage + 5 * s;
+  float* mu_now = c->stage + 6 * s;
+  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, phi_now, c->geo, read_pattern(c), c->stream));
+  LBM_CK(c, lbm::launch_mu(phi_now, mu_now, c->geo, c->ph, c->stream));
+  if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
+    LBM_CK(c, lbm::launch_fields(cur_state(c), phi_now, mu_now, c->stage, c->geo, c->ph,
+                                 read_pattern(c), velocity_time_factor(c, c->step), c->stream));
   std::vector<float> tmp;
   lbm_status st = LBM_OK;
-  if (mask & LBM_FIELD_PHI) st = plane_to_host(c, c->phi, phi, tmp);
-  if (st == LBM_OK && (mask & LBM_FIELD_MU)) st = plane_to_host(c, c->mu, mu, tmp);
+  if (mask & LBM_FIELD_PHI) st = plane_to_host(c, phi_now, phi, tmp);
+  if (st == LBM_OK && (mask & LBM_FIELD_MU)) st = plane_to_host(c, mu_now, mu, tmp);
   if (st == LBM_OK && (mask & LBM_FIELD_RHO)) st = plane_to_host(c, c->stage, rho, tmp);
   if (st == LBM_OK && (mask & LBM_FIELD_P)) st = plane_to_host(c, c->stage + s, p, tmp);
   for (int a = 0; a < 3 && st == LBM_OK && (mask & LBM_FIELD_U); ++a)
@@ -369,8 +379,9 @@ lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
   if (!c) return LBM_EINVAL;
   if (!sum_phi || !mom) return fail(c, LBM_EINVAL, "outputs must not be NULL");
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
-  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, c->geo, read_pattern(c), c->stream));
-  LBM_CK(c, lbm::launch_reduce(cur_state(c), c->phi, c->partial, c->red, c->geo, read_pattern(c),
+  float* phi_now = c->stage + 5 * c->geo.stride;
+  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, phi_now, c->geo, read_pattern(c), c->stream));
+  LBM_CK(c, lbm::launch_reduce(cur_state(c), phi_now, c->partial, c->red, c->geo, read_pattern(c),
                                c->vel_kind == LBM_VELOCITY_NONE, c->stream));
   double h[5];
   LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -397,7 +408,8 @@ lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long
     else
       dst = (phiu_prev && c->have_prev) ? phiu_prev + (q - lbm::kSlotPhiu) * n : nullptr;
     if (!dst) continue;
-    LBM_CK(c, lbm::launch_gather(cur_state(c), c->stage, c->geo, read_pattern(c), q, c->stream));
+    LBM_CK(c, lbm::launch_gather(cur_state(c), c->phi, c->stage, c->geo, read_pattern(c), q,
+                                 c->stream));
     LBM_CK(c, cudaMemcpyAsync(dst, c->stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   }
   if (phiu_prev && !c->have_prev) std::memset(phiu_prev, 0, 3 * n * sizeof(float));
@@ -424,7 +436,13 @@ lbm_status lbm_write_state(lbm_ctx* c, const float* f, const float* g, const flo
     else if (prev)
       src = phiu_prev + (q - lbm::kSlotPhiu) * n;
     if (!src) continue;
-    LBM_CK(c, cudaMemcpyAsync(c->stage, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    if (q == 0 && c->geo.storage != LBM_STORAGE_FP32) {
+      // 16-bit storage: f_0 becomes the reference phi, slot 0 holds f_0 - phi = 0
+      LBM_CK(c, cudaMemcpyAsync(c->phi, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+      LBM_CK(c, cudaMemsetAsync(c->stage, 0, n * sizeof(float), c->stream));
+    } else {
+      LBM_CK(c, cudaMemcpyAsync(c->stage, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    }
     LBM_CK(c, lbm::launch_scatter(cur_state(c), c->stage, c->geo, read_pattern(c), q, c->stream));
   }
   LBM_CK(c, cudaStreamSynchronize(c->stream));

@@ -5,6 +5,9 @@
 // rather than as dense products.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -30,6 +33,7 @@ struct Geometry {
   FastDiv div_nx, div_ny;
   int prefetch_collide;  // L2 prefetch distance of k_collide in blocks (0: none)
   int prefetch_phi;      // same for k_phi
+  int storage;           // population storage type (Storage); selects the kernel instance
 };
 
 __device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
@@ -73,20 +77,73 @@ constexpr int kSlotPhiu = kSlots;     // first phi u slot
 constexpr int kTileSlots = kSlots + 3;
 
 // Cell-state layout: tiles of kTile consecutive cells (x fastest); a tile stores its
-// 25 slots one after another, kTile floats each (3.2 KB per tile).  A warp's own-cell
-// accesses therefore fall in one small block of memory instead of 25 arrays a whole
-// grid apart, which keeps the number of pages a warp touches small.
+// 25 slots one after another, kTile values each: the 22 populations in the storage
+// type (FP32, FP16 or BF16), then the 3 phi u components in FP32 (3.2 KB per tile in
+// FP32, 1.75 KB with 16-bit populations).  A warp's own-cell accesses therefore fall
+// in one small block of memory instead of 25 arrays a whole grid apart, which keeps
+// the number of pages a warp touches small.
 constexpr int kTile = 32;
 constexpr int kTileShift = 5;
 
-__device__ __forceinline__ size_t tile_base(int i) {
-  return static_cast<size_t>(i >> kTileShift) * (kTileSlots * kTile) + (i & (kTile - 1));
+// Population storage types.  With 16-bit storage, slot 0 holds f_0 - phi (phi of the
+// step that wrote it, kept in the order-parameter array) instead of f_0 ~ phi ~ +-1,
+// which 16 bits would round to ~1e-3; all arithmetic stays FP32.
+enum Storage { kF32 = 0, kF16 = 1, kBF16 = 2 };
+
+template <int S>
+struct Elem;
+template <>
+struct Elem<kF32> {
+  typedef float T;
+  static __device__ __forceinline__ float get(T v) { return v; }
+  static __device__ __forceinline__ T put(float v) { return v; }
+};
+template <>
+struct Elem<kF16> {
+  typedef __half T;
+  static __device__ __forceinline__ float get(T v) { return __half2float(v); }
+  static __device__ __forceinline__ T put(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Elem<kBF16> {
+  typedef __nv_bfloat16 T;
+  static __device__ __forceinline__ float get(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ T put(float v) { return __float2bfloat16_rn(v); }
+};
+
+template <int S>
+__host__ __device__ constexpr int tile_bytes() {
+  return kSlots * kTile * static_cast<int>(sizeof(typename Elem<S>::T)) + 3 * kTile * 4;
 }
 
-template <int SLOT>
-__device__ __forceinline__ size_t slot_addr(int i) {
-  return tile_base(i) + SLOT * kTile;
+// Start of the tile holding cell i (as a float pointer: tiles are 16-byte multiples).
+template <int S>
+__device__ __forceinline__ size_t tile_floats(int i) {
+  return static_cast<size_t>(i >> kTileShift) * (tile_bytes<S>() / 4);
 }
+
+template <int S, int SLOT>
+__device__ __forceinline__ typename Elem<S>::T* pop_ptr(float* state, int i) {
+  typedef typename Elem<S>::T T;
+  return reinterpret_cast<T*>(state + tile_floats<S>(i)) + SLOT * kTile + (i & (kTile - 1));
+}
+
+template <int S, int SLOT>
+__device__ __forceinline__ const typename Elem<S>::T* pop_ptr(const float* state, int i) {
+  typedef typename Elem<S>::T T;
+  return reinterpret_cast<const T*>(state + tile_floats<S>(i)) + SLOT * kTile + (i & (kTile - 1));
+}
+
+// phi u component a of cell i
+template <int S>
+__device__ __forceinline__ size_t phiu_index(int i, int a) {
+  return tile_floats<S>(i) + (kSlots * kTile * sizeof(typename Elem<S>::T)) / 4 + a * kTile +
+         (i & (kTile - 1));
+}
+
+// FP32 layout helpers (slot of cell i as a float index), used where the storage type
+// is FP32 by construction.
+__device__ __forceinline__ size_t tile_base(int i) { return tile_floats<kF32>(i) + (i & (kTile - 1)); }
 
 // ---------------------------------------------------------------------------------
 // Neighbour offsets of one cell.  x and y wrap; z wraps or, between walls, the
@@ -145,54 +202,57 @@ __device__ __forceinline__ int offset(const Nbr& nb) {
 // ---------------------------------------------------------------------------------
 enum Pattern { kAB = 0, kAAEven = 1, kAAOdd = 2 };
 
-template <int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+template <int S, int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
 __device__ __forceinline__ float pop_load(const float* a, int idx, const Nbr& nb) {
-  if (P == kAAEven) return a[slot_addr<SLOT>(idx)];
+  typedef Elem<S> E;
+  if (P == kAAEven) return E::get(*pop_ptr<S, SLOT>(a, idx));
   const bool wall = (CZ > 0 && nb.wlo) || (CZ < 0 && nb.whi);
   if (P == kAAOdd) {
-    if (wall) return a[slot_addr<SLOT>(idx)];
-    return a[slot_addr<SLOT_OPP>(idx + offset<-CX, -CY, -CZ>(nb))];
+    if (wall) return E::get(*pop_ptr<S, SLOT>(a, idx));
+    return E::get(*pop_ptr<S, SLOT_OPP>(a, idx + offset<-CX, -CY, -CZ>(nb)));
   }
-  if (wall) return a[slot_addr<SLOT_OPP>(idx)];
-  return a[slot_addr<SLOT>(idx + offset<-CX, -CY, -CZ>(nb))];
+  if (wall) return E::get(*pop_ptr<S, SLOT_OPP>(a, idx));
+  return E::get(*pop_ptr<S, SLOT>(a, idx + offset<-CX, -CY, -CZ>(nb)));
 }
 
 // Store the post-collision value of direction SLOT of cell idx.
-template <int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+template <int S, int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
 __device__ __forceinline__ void pop_store(float* a, int idx, const Nbr& nb, float v) {
+  typedef Elem<S> E;
   if (P == kAB) {
-    a[slot_addr<SLOT>(idx)] = v;
+    *pop_ptr<S, SLOT>(a, idx) = E::put(v);
   } else if (P == kAAEven) {
-    a[slot_addr<SLOT_OPP>(idx)] = v;
+    *pop_ptr<S, SLOT_OPP>(a, idx) = E::put(v);
   } else {
     const bool wall = (CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo);
     if (wall)
-      a[slot_addr<SLOT_OPP>(idx)] = v;
+      *pop_ptr<S, SLOT_OPP>(a, idx) = E::put(v);
     else
-      a[slot_addr<SLOT>(idx + offset<CX, CY, CZ>(nb))] = v;
+      *pop_ptr<S, SLOT>(a, idx + offset<CX, CY, CZ>(nb)) = E::put(v);
   }
 }
 
 // Place the PRE-collision value of direction SLOT of cell idx where a step of pattern
 // P reads it (inverse of pop_load): used to write initial and restored states.
-template <int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
+template <int S, int P, int SLOT, int SLOT_OPP, int CX, int CY, int CZ>
 __device__ __forceinline__ void pop_place(float* a, int idx, const Nbr& nb, float v) {
+  typedef Elem<S> E;
   if (P == kAAEven) {
-    a[slot_addr<SLOT>(idx)] = v;
+    *pop_ptr<S, SLOT>(a, idx) = E::put(v);
     return;
   }
   const bool wall = (CZ > 0 && nb.wlo) || (CZ < 0 && nb.whi);
   if (P == kAAOdd) {
     if (wall)
-      a[slot_addr<SLOT>(idx)] = v;
+      *pop_ptr<S, SLOT>(a, idx) = E::put(v);
     else
-      a[slot_addr<SLOT_OPP>(idx + offset<-CX, -CY, -CZ>(nb))] = v;
+      *pop_ptr<S, SLOT_OPP>(a, idx + offset<-CX, -CY, -CZ>(nb)) = E::put(v);
     return;
   }
   if (wall)
-    a[slot_addr<SLOT_OPP>(idx)] = v;
+    *pop_ptr<S, SLOT_OPP>(a, idx) = E::put(v);
   else
-    a[slot_addr<SLOT>(idx + offset<-CX, -CY, -CZ>(nb))] = v;
+    *pop_ptr<S, SLOT>(a, idx + offset<-CX, -CY, -CZ>(nb)) = E::put(v);
 }
 
 // D3Q7 velocities (Eq. 6) as template arguments: slot, opposite slot, c.
@@ -223,44 +283,44 @@ __device__ __forceinline__ void pop_place(float* a, int idx, const Nbr& nb, floa
   X(13, 14, 1, -1, -1)    \
   X(14, 13, -1, 1, 1)
 
-template <int P>
+template <int P, int S = kF32>
 __device__ __forceinline__ void load_f(const float* a, int idx, const Nbr& nb, float f[7]) {
-#define X(I, O, CX, CY, CZ) f[I] = pop_load<P, I, O, CX, CY, CZ>(a, idx, nb);
+#define X(I, O, CX, CY, CZ) f[I] = pop_load<S, P, I, O, CX, CY, CZ>(a, idx, nb);
   LBM_D3Q7_LIST(X)
 #undef X
 }
 
-template <int P>
+template <int P, int S = kF32>
 __device__ __forceinline__ void store_f(float* a, int idx, const Nbr& nb, const float f[7]) {
-#define X(I, O, CX, CY, CZ) pop_store<P, I, O, CX, CY, CZ>(a, idx, nb, f[I]);
+#define X(I, O, CX, CY, CZ) pop_store<S, P, I, O, CX, CY, CZ>(a, idx, nb, f[I]);
   LBM_D3Q7_LIST(X)
 #undef X
 }
 
-template <int P>
+template <int P, int S = kF32>
 __device__ __forceinline__ void place_f(float* a, int idx, const Nbr& nb, const float f[7]) {
-#define X(I, O, CX, CY, CZ) pop_place<P, I, O, CX, CY, CZ>(a, idx, nb, f[I]);
+#define X(I, O, CX, CY, CZ) pop_place<S, P, I, O, CX, CY, CZ>(a, idx, nb, f[I]);
   LBM_D3Q7_LIST(X)
 #undef X
 }
 
-template <int P>
+template <int P, int S = kF32>
 __device__ __forceinline__ void load_g(const float* a, int idx, const Nbr& nb, float g[15]) {
-#define X(I, O, CX, CY, CZ) g[I] = pop_load<P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb);
+#define X(I, O, CX, CY, CZ) g[I] = pop_load<S, P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb);
   LBM_D3Q15_LIST(X)
 #undef X
 }
 
-template <int P>
+template <int P, int S = kF32>
 __device__ __forceinline__ void store_g(float* a, int idx, const Nbr& nb, const float g[15]) {
-#define X(I, O, CX, CY, CZ) pop_store<P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb, g[I]);
+#define X(I, O, CX, CY, CZ) pop_store<S, P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb, g[I]);
   LBM_D3Q15_LIST(X)
 #undef X
 }
 
-template <int P>
+template <int P, int S = kF32>
 __device__ __forceinline__ void place_g(float* a, int idx, const Nbr& nb, const float g[15]) {
-#define X(I, O, CX, CY, CZ) pop_place<P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb, g[I]);
+#define X(I, O, CX, CY, CZ) pop_place<S, P, 7 + I, 7 + O, CX, CY, CZ>(a, idx, nb, g[I]);
   LBM_D3Q15_LIST(X)
 #undef X
 }
@@ -531,15 +591,19 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
 //   m+ = m - S (m - m^eq) + (I - S/2) mR,   f+ = M^{-1} m+
 // again applied as f+ = f - M^{-1} Delta; |row|^2 of M = 7, 2, 2, 2, 42, 12, 4.
 // ---------------------------------------------------------------------------------
+// With SHIFT0 (16-bit storage) f[0] is not read: f_0 = phi - sum_{i>0} f_i, so
+// m_0 = phi and m_4 = 6 phi - 7 sum_{i>0} f_i; on return f[0] holds f_0^+ - phi.
+template <bool SHIFT0 = false>
 __device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], float phi, float mu,
                                              const float u[3], const float dphiu[3]) {
   const float sx = f[1] + f[2], sy = f[3] + f[4], sz = f[5] + f[6];
+  const float smov = sx + sy + sz;
   float m[7];
-  m[0] = f[0] + (sx + sy + sz);
+  m[0] = SHIFT0 ? phi : f[0] + smov;
   m[1] = f[1] - f[2];
   m[2] = f[3] - f[4];
   m[3] = f[5] - f[6];
-  m[4] = 6.0f * f[0] - (sx + sy + sz);
+  m[4] = SHIFT0 ? 6.0f * phi - 7.0f * smov : 6.0f * f[0] - smov;
   m[5] = 2.0f * sx - sy - sz;
   m[6] = sy - sz;
   const float meq[7] = {phi, phi * u[0], phi * u[1], phi * u[2],
@@ -553,7 +617,10 @@ __device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], floa
     b[k] = (s * (m[k] - meq[k]) - (1.0f - 0.5f * s) * mR[k]) * inv_n[k];
   }
   const float e = b[0] - b[4];
-  f[0] -= b[0] + 6.0f * b[4];
+  if (SHIFT0)
+    f[0] = -(smov + (b[0] + 6.0f * b[4]));
+  else
+    f[0] -= b[0] + 6.0f * b[4];
   const float ex = e + 2.0f * b[5];
   f[1] -= ex + b[1];
   f[2] -= ex - b[1];

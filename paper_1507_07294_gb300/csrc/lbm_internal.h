@@ -15,8 +15,9 @@ void set_global_error(const std::string& msg);
 // Upper bound on the number of per-block partial sums of the FP64 reduction.
 constexpr int kReduceMaxParts = 1024;
 
-cudaError_t launch_phi(const float* src, float* phi, const Geometry& geo, int pattern,
-                       cudaStream_t st);
+// phi_ref: order parameter of the previous step (read by 16-bit storage); may equal phi.
+cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const Geometry& geo,
+                       int pattern, cudaStream_t st);
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st);
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
@@ -31,26 +32,27 @@ cudaError_t launch_fields(const float* src, const float* phi, const float* mu, f
 cudaError_t launch_init(float* state, const float* phi, const float* mu, const float* u0,
                         const float* p0, const Geometry& geo, const Physics& ph, int pattern,
                         float tf, cudaStream_t st);
-cudaError_t launch_gather(const float* src, float* dense, const Geometry& geo, int pattern,
-                          int slot, cudaStream_t st);
+cudaError_t launch_gather(const float* src, const float* phi_ref, float* dense, const Geometry& geo,
+                          int pattern, int slot, cudaStream_t st);
 cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
                            int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
 // Resident blocks per SM of k_collide (kernel 0) or k_phi (kernel 1); 0 on error.
-int resident_blocks_per_sm(int kernel);
+int resident_blocks_per_sm(int kernel, int storage);
 cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
                           const Geometry& geo, int pattern, bool with_g, cudaStream_t st);
-// Floats of the tiled cell-state array for n cells.
-inline size_t state_floats(int n) {
-  return static_cast<size_t>((n + kTile - 1) / kTile) * kTileSlots * kTile;
+// Bytes of the tiled cell-state array for n cells.
+inline size_t state_bytes(int n, int storage) {
+  const int tb = storage == kF32 ? tile_bytes<kF32>() : tile_bytes<kF16>();
+  return static_cast<size_t>((n + kTile - 1) / kTile) * tb;
 }
 cudaError_t launch_gather(const float* pop, float* dense, const Geometry& geo, bool odd,
                           int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
 // Resident blocks per SM of k_collide (kernel 0) or k_phi (kernel 1); 0 on error.
-int resident_blocks_per_sm(int kernel);
+int resident_blocks_per_sm(int kernel, int storage);
 cudaError_t launch_reduce(const float* pop, const float* phi, double* partial, double* out,
                           const Geometry& geo, bool odd, cudaStream_t st);
 

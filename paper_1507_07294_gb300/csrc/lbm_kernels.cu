@@ -38,7 +38,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // (dist = one wave: SMs x resident blocks per SM).  k_collide prefetches the whole cell
 // state of those cells (all 25 slots) and their phi and mu; k_phi only the 7 f slots of
 // each tile.  All ranges are clipped to the arrays.
-template <bool ALL_SLOTS>
+template <int S, bool ALL_SLOTS>
 __device__ __forceinline__ void prefetch_ahead(const float* state, const float* phi, const float* mu,
                                                const Geometry& geo, int dist) {
   if (dist <= 0 || threadIdx.x != 0) return;
@@ -47,9 +47,9 @@ __device__ __forceinline__ void prefetch_ahead(const float* state, const float* 
   const long long cells = min(static_cast<long long>(kBlock), geo.n - first);
   // kBlock is a multiple of kTile, so `first` starts a tile
   const int tiles = static_cast<int>((cells + kTile - 1) / kTile);
-  const float* t0 = state + tile_base(static_cast<int>(first));
+  const float* t0 = state + tile_floats<S>(static_cast<int>(first));
   if (ALL_SLOTS) {
-    prefetch_l2(t0, static_cast<unsigned>(tiles * kTileSlots * kTile * sizeof(float)));
+    prefetch_l2(t0, static_cast<unsigned>(tiles * tile_bytes<S>()));
     const unsigned bytes = static_cast<unsigned>(cells * sizeof(float)) & ~15u;
     if (bytes) {
       prefetch_l2(phi + first, bytes);
@@ -57,22 +57,27 @@ __device__ __forceinline__ void prefetch_ahead(const float* state, const float* 
     }
   } else {
     for (int t = 0; t < tiles; ++t)
-      prefetch_l2(t0 + t * (kTileSlots * kTile), kQ7 * kTile * sizeof(float));
+      prefetch_l2(t0 + t * (tile_bytes<S>() / 4),
+                  static_cast<unsigned>(kQ7 * kTile * sizeof(typename Elem<S>::T)));
   }
 }
 
 // ------------------------------------------------------------------ k_phi ---------
-template <int P>
+// With 16-bit storage slot 0 holds f_0 - phi_ref, phi_ref the order parameter of the
+// step that wrote it; phi_ref and phi may be the same array (each thread reads its own
+// cell before writing it).
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
-                                                float* __restrict__ phi, Geometry geo) {
-  prefetch_ahead<false>(src, nullptr, nullptr, geo, geo.prefetch_phi);
+                                                const float* phi_ref, float* phi, Geometry geo) {
+  prefetch_ahead<S, false>(src, nullptr, nullptr, geo, geo.prefetch_phi);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
   int x, y, z;
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
   float f[7];
-  load_f<P>(src, idx, nb, f);
+  load_f<P, S>(src, idx, nb, f);
+  if (S != kF32) f[0] += phi_ref[idx];
   phi[idx] = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]));
 }
 
@@ -178,11 +183,11 @@ __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ 
 #define LBM_COLLIDE_MIN_BLOCKS 3
 #endif
 
-template <int P, int VAR>
+template <int P, int VAR, int S>
 __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
     k_collide(const float* src, float* dst, const float* __restrict__ phi,
               const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev) {
-  prefetch_ahead<true>(src, phi, mu, geo, geo.prefetch_collide);
+  prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
   int x, y, z;
@@ -190,17 +195,16 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
   const Nbr nb = make_nbr(geo, x, y, z);
 
   float g[15], f[7], prev[3];
-  load_g<P>(src, idx, nb, g);
-  load_f<P>(src, idx, nb, f);
-  const size_t own = tile_base(idx) + kSlotPhiu * kTile;
+  load_g<P, S>(src, idx, nb, g);
+  load_f<P, S>(src, idx, nb, f);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) prev[a] = src[own + a * kTile];
+  for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
 
   const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
   collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
-  store_g<P>(dst, idx, nb, g);
+  store_g<P, S>(dst, idx, nb, g);
 
   // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
   float dphiu[3];
@@ -208,18 +212,18 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
   for (int a = 0; a < 3; ++a) {
     const float cur = cs.phi * M.u[a];
     dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
-    dst[own + a * kTile] = cur;
+    dst[phiu_index<S>(idx, a)] = cur;
   }
 
-  collide_d3q7(ph, f, cs.phi, cs.mu, M.u, dphiu);
-  store_f<P>(dst, idx, nb, f);
+  collide_d3q7<S != kF32>(ph, f, cs.phi, cs.mu, M.u, dphiu);
+  store_f<P, S>(dst, idx, nb, f);
 }
 
 // ------------------------------------------------------------------ k_che ---------
 // Interface tracking with a prescribed velocity (Sec. III A, B): only the D3Q7 lattice
 // evolves (Eq. 4); u is analytic, so the flow lattice and the stencils of phi and mu
 // are not needed.  tf is the time factor of the velocity field at this step.
-template <int P>
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_che(const float* src, float* dst,
                                                 const float* __restrict__ phi,
                                                 const float* __restrict__ mu, Geometry geo,
@@ -230,10 +234,9 @@ __global__ void __launch_bounds__(kBlock) k_che(const float* src, float* dst,
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
   float f[7], prev[3];
-  load_f<P>(src, idx, nb, f);
-  const size_t own = tile_base(idx) + kSlotPhiu * kTile;
+  load_f<P, S>(src, idx, nb, f);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) prev[a] = src[own + a * kTile];
+  for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
   const float phi_c = __ldg(phi + idx), mu_c = __ldg(mu + idx);
   float u[3];
   prescribed_velocity(ph, geo, x, y, z, tf, u);
@@ -242,15 +245,15 @@ __global__ void __launch_bounds__(kBlock) k_che(const float* src, float* dst,
   for (int a = 0; a < 3; ++a) {
     const float cur = phi_c * u[a];
     dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
-    dst[own + a * kTile] = cur;
+    dst[phiu_index<S>(idx, a)] = cur;
   }
-  collide_d3q7(ph, f, phi_c, mu_c, u, dphiu);
-  store_f<P>(dst, idx, nb, f);
+  collide_d3q7<S != kF32>(ph, f, phi_c, mu_c, u, dphiu);
+  store_f<P, S>(dst, idx, nb, f);
 }
 
 // --------------------------------------------------------------- k_fields ---------
 // rho, p, u of the current populations into out[0..4] (rho, p, ux, uy, uz).
-template <int P>
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src,
                                                    const float* __restrict__ phi,
                                                    const float* __restrict__ mu,
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src
   const CellStencils cs = ph.d3q7_stencil ? cell_stencils<true>(phi, mu, idx, nb)
                                           : cell_stencils<false>(phi, mu, idx, nb);
   float g[15];
-  load_g<P>(src, idx, nb, g);
+  load_g<P, S>(src, idx, nb, g);
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   out[0 * s + idx] = M.rho;
   out[1 * s + idx] = M.p;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src
 // ------------------------------------------------------------------ k_init --------
 // Pre-collision populations f = f^eq (Eq. 5), g = g^eq (Eq. 21) placed for a step of
 // pattern P; phi u stored in the own tile.  u0 (3 dense planes) and p0 may be null.
-template <int P>
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __restrict__ phi,
                                                  const float* __restrict__ mu,
                                                  const float* __restrict__ u0,
@@ -315,8 +318,10 @@ __global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __re
   const float emu = ph.eta * mu_;
   const float hw = 0.5f * ph.A * emu;
   const float jx = 0.5f * ph_ * u[0], jy = 0.5f * ph_ * u[1], jz = 0.5f * ph_ * u[2];
-  const float f[7] = {ph_ - 3.0f * ph.A * emu, hw + jx, hw - jx, hw + jy, hw - jy, hw + jz, hw - jz};
-  place_f<P>(state, idx, nb, f);
+  // 16-bit storage keeps f_0 - phi in slot 0
+  const float f0 = S != kF32 ? -3.0f * ph.A * emu : ph_ - 3.0f * ph.A * emu;
+  const float f[7] = {f0, hw + jx, hw - jx, hw + jy, hw - jy, hw + jz, hw - jz};
+  place_f<P, S>(state, idx, nb, f);
 
   // D3Q15: g_i = 3 p omega_i + rho omega_i (3 c.u + 9/2 (c.u)^2 - 3/2 u^2), g_0 -= 3p
   const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -331,18 +336,18 @@ __global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __re
     g[i] = 3.0f * p * w + rho * w * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
   }
   g[0] -= 3.0f * p;
-  place_g<P>(state, idx, nb, g);
-  const size_t own = tile_base(idx) + kSlotPhiu * kTile;
-  state[own + 0 * kTile] = ph_ * u[0];
-  state[own + 1 * kTile] = ph_ * u[1];
-  state[own + 2 * kTile] = ph_ * u[2];
+  place_g<P, S>(state, idx, nb, g);
+  state[phiu_index<S>(idx, 0)] = ph_ * u[0];
+  state[phiu_index<S>(idx, 1)] = ph_ * u[1];
+  state[phiu_index<S>(idx, 2)] = ph_ * u[2];
 }
 
 // -------------------------------------------------- state gather / scatter --------
 // Slot `slot` of the current pre-collision state to dense[idx]: populations through
 // the pattern's addressing, phi u (slots 22..24) from the own tile.
-template <int P>
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ src,
+                                                   const float* __restrict__ phi_ref,
                                                    float* __restrict__ dense, Geometry geo,
                                                    int slot) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
@@ -354,25 +359,28 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ src
   switch (slot) {
 #define X(I, O, CX, CY, CZ) \
   case I:                   \
-    v = pop_load<P, I, O, CX, CY, CZ>(src, idx, nb); \
+    v = pop_load<S, P, I, O, CX, CY, CZ>(src, idx, nb); \
     break;
     LBM_D3Q7_LIST(X)
 #undef X
 #define X(I, O, CX, CY, CZ) \
   case 7 + I:               \
-    v = pop_load<P, 7 + I, 7 + O, CX, CY, CZ>(src, idx, nb); \
+    v = pop_load<S, P, 7 + I, 7 + O, CX, CY, CZ>(src, idx, nb); \
     break;
     LBM_D3Q15_LIST(X)
 #undef X
     default:
-      v = src[tile_base(idx) + slot * kTile];
+      v = src[phiu_index<S>(idx, slot - kSlotPhiu)];
   }
+  if (S != kF32 && slot == 0) v += phi_ref[idx];
   dense[idx] = v;
 }
 
 // dense[idx] = pre-collision value of slot `slot` of cell idx, placed where a step of
 // pattern P reads it (the inverse of k_gather).
-template <int P>
+// (With 16-bit storage the caller writes f_0 into the order-parameter array and
+// scatters zeros into slot 0.)
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_scatter(float* state, const float* __restrict__ dense,
                                                     Geometry geo, int slot) {
   const int idx = blockIdx.x * kBlock + threadIdx.x;
@@ -384,18 +392,18 @@ __global__ void __launch_bounds__(kBlock) k_scatter(float* state, const float* _
   switch (slot) {
 #define X(I, O, CX, CY, CZ) \
   case I:                   \
-    pop_place<P, I, O, CX, CY, CZ>(state, idx, nb, v); \
+    pop_place<S, P, I, O, CX, CY, CZ>(state, idx, nb, v); \
     break;
     LBM_D3Q7_LIST(X)
 #undef X
 #define X(I, O, CX, CY, CZ) \
   case 7 + I:               \
-    pop_place<P, 7 + I, 7 + O, CX, CY, CZ>(state, idx, nb, v); \
+    pop_place<S, P, 7 + I, 7 + O, CX, CY, CZ>(state, idx, nb, v); \
     break;
     LBM_D3Q15_LIST(X)
 #undef X
     default:
-      state[tile_base(idx) + slot * kTile] = v;
+      state[phiu_index<S>(idx, slot - kSlotPhiu)] = v;
   }
 }
 
@@ -410,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_convert(const double* __restrict__ i
 // order: grid-stride rows, then a fixed shuffle tree).
 // partial[b] = {sum phi, jx, jy, jz, non-finite count}.
 // with_g = 0 (tracking mode, no flow lattice): the momentum sums are zero.
-template <int P>
+template <int P, int S>
 __global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restrict__ src,
                                                            const float* __restrict__ phi,
                                                            double* __restrict__ partial,
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restri
       cell_coords(geo, idx, x, y, z);
       const Nbr nb = make_nbr(geo, x, y, z);
       float g[15];
-      load_g<P>(src, idx, nb, g);
+      load_g<P, S>(src, idx, nb, g);
       const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12], d13 = g[13] - g[14];
       jx = (g[1] - g[2]) + ((d7 + d9) + (d11 + d13));
       jy = (g[3] - g[4]) + ((d7 + d9) - (d11 + d13));
@@ -472,23 +480,29 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double* __restric
 
 inline unsigned blocks_for(int n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
-// Host-side dispatch of a kernel template over the three patterns.
-#define LBM_DISPATCH(pattern, KERNEL, ...)                                          \
-  do {                                                                            \
-    if ((pattern) == kAB)                                                         \
-      KERNEL<kAB><<<blocks_for(geo.n), kBlock, 0, st>>>(__VA_ARGS__);             \
-    else if ((pattern) == kAAEven)                                                \
-      KERNEL<kAAEven><<<blocks_for(geo.n), kBlock, 0, st>>>(__VA_ARGS__);         \
-    else                                                                          \
-      KERNEL<kAAOdd><<<blocks_for(geo.n), kBlock, 0, st>>>(__VA_ARGS__);          \
+// Host-side dispatch of a kernel template over the pattern (FP32 storage) or the
+// 16-bit storage types (pattern AB only).
+#define LBM_DISPATCH(geo, pattern, KERNEL, ...)                                          \
+  do {                                                                                   \
+    const unsigned blocks_ = blocks_for((geo).n);                                         \
+    if ((geo).storage == kF16)                                                           \
+      KERNEL<kAB, kF16><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                       \
+    else if ((geo).storage == kBF16)                                                     \
+      KERNEL<kAB, kBF16><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                      \
+    else if ((pattern) == kAB)                                                           \
+      KERNEL<kAB, kF32><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                       \
+    else if ((pattern) == kAAEven)                                                       \
+      KERNEL<kAAEven, kF32><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                   \
+    else                                                                                 \
+      KERNEL<kAAOdd, kF32><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                    \
   } while (0)
 
 }  // namespace
 
 // ------------------------------------------------------------ host launchers ------
-cudaError_t launch_phi(const float* src, float* phi, const Geometry& geo, int pattern,
-                       cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_phi, src, phi, geo);
+cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const Geometry& geo,
+                       int pattern, cudaStream_t st) {
+  LBM_DISPATCH(geo, pattern, k_phi, src, phi_ref, phi, geo);
   return cudaGetLastError();
 }
 
@@ -507,12 +521,16 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
                      const Geometry& geo, const Physics& ph, int pattern, int prev,
                      cudaStream_t st) {
   const unsigned blocks = blocks_for(geo.n);
-  if (pattern == kAB)
-    k_collide<kAB, VAR><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+  if (geo.storage == kF16)
+    k_collide<kAB, VAR, kF16><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+  else if (geo.storage == kBF16)
+    k_collide<kAB, VAR, kBF16><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+  else if (pattern == kAB)
+    k_collide<kAB, VAR, kF32><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
   else if (pattern == kAAEven)
-    k_collide<kAAEven, VAR><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+    k_collide<kAAEven, VAR, kF32><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
   else
-    k_collide<kAAOdd, VAR><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+    k_collide<kAAOdd, VAR, kF32><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
 }
 
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
@@ -533,33 +551,33 @@ cudaError_t launch_collide(const float* src, float* dst, const float* phi, const
 cudaError_t launch_che(const float* src, float* dst, const float* phi, const float* mu,
                        const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                        float tf, cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_che, src, dst, phi, mu, geo, ph, have_prev ? 1 : 0, tf);
+  LBM_DISPATCH(geo, pattern, k_che, src, dst, phi, mu, geo, ph, have_prev ? 1 : 0, tf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fields(const float* src, const float* phi, const float* mu, float* out,
                           const Geometry& geo, const Physics& ph, int pattern, float tf,
                           cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_fields, src, phi, mu, out, geo, ph, tf);
+  LBM_DISPATCH(geo, pattern, k_fields, src, phi, mu, out, geo, ph, tf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_init(float* state, const float* phi, const float* mu, const float* u0,
                         const float* p0, const Geometry& geo, const Physics& ph, int pattern,
                         float tf, cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_init, state, phi, mu, u0, p0, geo, ph, tf);
+  LBM_DISPATCH(geo, pattern, k_init, state, phi, mu, u0, p0, geo, ph, tf);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const float* src, float* dense, const Geometry& geo, int pattern,
-                          int slot, cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_gather, src, dense, geo, slot);
+cudaError_t launch_gather(const float* src, const float* phi_ref, float* dense, const Geometry& geo,
+                          int pattern, int slot, cudaStream_t st) {
+  LBM_DISPATCH(geo, pattern, k_gather, src, phi_ref, dense, geo, slot);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
                            int slot, cudaStream_t st) {
-  LBM_DISPATCH(pattern, k_scatter, state, dense, geo, slot);
+  LBM_DISPATCH(geo, pattern, k_scatter, state, dense, geo, slot);
   return cudaGetLastError();
 }
 
@@ -568,11 +586,15 @@ cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st)
   return cudaGetLastError();
 }
 
-int resident_blocks_per_sm(int kernel) {
+int resident_blocks_per_sm(int kernel, int storage) {
   int blocks = 0;
-  cudaError_t e = kernel == 0
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0>, kBlock, 0)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi<kAB>, kBlock, 0);
+  cudaError_t e;
+  if (kernel == 0)
+    e = storage == kF16    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kF16>, kBlock, 0)
+        : storage == kBF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kBF16>, kBlock, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kF32>, kBlock, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi<kAB, kF32>, kBlock, 0);
   return e == cudaSuccess ? blocks : 0;
 }
 
@@ -585,12 +607,16 @@ cudaError_t launch_reduce(const float* src, const float* phi, double* partial, d
                           const Geometry& geo, int pattern, bool with_g, cudaStream_t st) {
   const int parts = reduce_parts(geo);
   const int wg = with_g ? 1 : 0;
-  if (pattern == kAB)
-    k_reduce_partial<kAB><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+  if (geo.storage == kF16)
+    k_reduce_partial<kAB, kF16><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+  else if (geo.storage == kBF16)
+    k_reduce_partial<kAB, kBF16><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+  else if (pattern == kAB)
+    k_reduce_partial<kAB, kF32><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
   else if (pattern == kAAEven)
-    k_reduce_partial<kAAEven><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+    k_reduce_partial<kAAEven, kF32><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
   else
-    k_reduce_partial<kAAOdd><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+    k_reduce_partial<kAAOdd, kF32><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_final<<<1, kBlock, 0, st>>>(partial, parts, out);

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_EUNSTABLE", 5: "LBM_ETIMEOUT", 6: "LBM_EBUSY"}
 
 LBM_FLAG_BUOYANCY, LBM_FLAG_SRT_FLOW, LBM_FLAG_D3Q7_STENCIL = 1, 2, 4
-LBM_STORAGE_FP32 = 0
+LBM_STORAGE_FP32, LBM_STORAGE_FP16, LBM_STORAGE_BF16 = 0, 1, 2
+STORAGES = {"fp32": LBM_STORAGE_FP32, "fp16": LBM_STORAGE_FP16, "bf16": LBM_STORAGE_BF16}
 LBM_PATTERN_AB, LBM_PATTERN_AA = 0, 1
 PATTERNS = {"ab": LBM_PATTERN_AB, "aa": LBM_PATTERN_AA}
 
@@ -135,15 +136,15 @@ def make_params(rho_l, rho_g, nu_l, nu_g, mobility, D, sigma, g=(0.0, 0.0, 0.0),
     p.sg[:] = [float(v) for v in sg]
     p.flags = ((LBM_FLAG_BUOYANCY if buoyancy else 0) | (LBM_FLAG_SRT_FLOW if srt_flow else 0)
                | (LBM_FLAG_D3Q7_STENCIL if stencil == "d3q7" else 0))
-    p.storage = storage
+    p.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
     p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
     return p
 
 
-def params_from_workload(w, pattern=LBM_PATTERN_AB) -> tuple:
+def params_from_workload(w, pattern=LBM_PATTERN_AB, storage=LBM_STORAGE_FP32) -> tuple:
     grid = LbmGrid(w.nx, w.ny, w.nz, 1 if w.walls_z else 0)
     params = make_params(w.rho_l, w.rho_g, w.nu_l, w.nu_g, w.mobility, w.D, w.sigma, w.g, w.A,
-                         w.sf, w.sg, w.buoyancy, pattern=pattern,
+                         w.sf, w.sg, w.buoyancy, pattern=pattern, storage=storage,
                          srt_flow=getattr(w, "srt_flow", False),
                          stencil=getattr(w, "stencil", "d3q15"))
     return grid, params
@@ -352,9 +353,9 @@ class Solver:
     """One simulation: create from a workload, initialise, step, read."""
 
     def __init__(self, workload, stream: Optional[int] = None, allocator: str = "torch",
-                 init: bool = True, pattern=LBM_PATTERN_AB):
+                 init: bool = True, pattern=LBM_PATTERN_AB, storage=LBM_STORAGE_FP32):
         self.workload = workload
-        grid, params = params_from_workload(workload, pattern)
+        grid, params = params_from_workload(workload, pattern, storage)
         self.ctx = lbm_create(grid, params, stream=stream, allocator=allocator)
         v = getattr(workload, "velocity", None)
         if v is not None:

@@ -68,6 +68,6 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     args = bench.main.__globals__["argparse"].Namespace(
         impl="reference", gpus=2, steps=5, warmup=3, workload="rt256", pattern="ab",
-        no_e2e=False, no_cpu_baseline=False, no_tune=False)
+        no_e2e=False, no_cpu_baseline=False, no_tune=False, no_variants=False)
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
