@@ -15,6 +15,10 @@ Printed JSON line (rank 0):
   roofline   the fused stream-collide kernel: algorithmic bytes per launch / its mean
              CUDA-event duration, against the measured HBM copy bandwidth.
   cpu_baseline  the FP64 oracle, single-threaded, on a bounded sample (rank 0, N = 1).
+  serving    the request loop: a seeded Poisson stream of Rayleigh-Taylor runs of
+             mixed grids served by continuous batching and one at a time; p50/p99
+             time to solution and aggregate MLUPS of each (step counts scaled by
+             --serve-scale, 0.1 by default, to keep the leg near a minute).
 With --impl reference the oracle alone is timed on the host cores (the reference arm).
 Under torchrun each rank runs an independent replica (weak scaling, no collective on
 the data path).
@@ -240,6 +244,56 @@ def config_dict(args, w, world):
             "parallelism": f"replicas x{world} (independent runs per GPU)"}
 
 
+# ------------------------------------------------------------ serving leg -------
+def run_serving(args, rank: int) -> dict:
+    """The continuous-batching request loop against one-at-a-time service, on the same
+    seeded Poisson request stream: grids 32^3, 64^3, 64x64x256, 128x128x512; Re, At,
+    sigma uniform; step counts uniform in [2000, 20000] x --serve-scale; arrivals
+    rescaled so the offered load is --serve-load x the one-at-a-time capacity measured
+    on this GPU; admission by a --serve-budget-gb device-memory budget."""
+    import torch
+    from paper_1507_07294_gb300 import serve as S
+
+    lo, hi = max(1, round(2000 * args.serve_scale)), max(1, round(20000 * args.serve_scale))
+    reqs = S.request_stream(args.serve_requests, seed=1000 + rank, steps=(lo, hi))
+    eng = S.GpuEngine()
+    # untimed: batch grid autotuning on one run per grid, per-grid service times alone
+    tuned = S.tune_batch(eng, S.GRIDS, quantum=args.serve_quantum)
+    model = S.service_time_model(eng, S.GRIDS, steps=200)
+    loaded = S.with_load(reqs, lambda r: model[r.grid][0] * r.steps + model[r.grid][1],
+                         args.serve_load)
+    budget = int(args.serve_budget_gb * 1e9)
+    res = {}
+    for name, batched in (("batched", True), ("one_at_a_time", False)):
+        srv = S.Server(eng, budget, max_runs=args.serve_slots, quantum=args.serve_quantum,
+                       batched=batched)
+        outs = srv.serve(loaded)
+        summ = S.summarize(outs)
+        by_rid = {r.rid: r for r in loaded}
+        bad = [by_rid[o.rid] for o in outs if not o.stable]
+        summ["unstable_by_grid"] = {"x".join(map(str, g)): sum(r.grid == g for r in bad)
+                                    for g in S.GRIDS}
+        summ["unstable_min_nu"] = (round(min(0.04 * r.grid[0] / r.re for r in bad), 6)
+                                   if bad else None)
+        summ.update(peak_runs=srv.peak_runs, peak_gb=round(srv.peak_bytes / 1e9, 3),
+                    quanta=srv.quanta)
+        res[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
+    eng.close()
+    return {
+        "requests": len(reqs), "grids": [list(g) for g in S.GRIDS],
+        "steps_range": [lo, hi], "re": [100, 4000], "atwood": [0.1, 0.9],
+        "sigma": [1e-3, 1e-2], "offered_load_x_one_at_a_time": args.serve_load,
+        "arrival_span_s": round(loaded[-1].arrival, 3), "budget_gb": args.serve_budget_gb,
+        "max_runs": args.serve_slots, "quantum_steps": args.serve_quantum,
+        "alone_ms_per_step": {"x".join(map(str, g)): round(v[0] * 1e3, 4)
+                              for g, v in model.items()},
+        "batch_tuning": {k: v for k, v in tuned.items() if not k.endswith("_ms")},
+        "time_to_solution": "arrival to phi and the FP64 sums on the host",
+        **res,
+        "mlups_ratio": round(res["batched"]["mlups"] / res["one_at_a_time"]["mlups"], 3),
+    }
+
+
 # ------------------------------------------------------------ reference arm -----
 def run_reference(args):
     world, rank, _ = dist_env()
@@ -393,6 +447,15 @@ def run_ours(args):
                 "step_bytes_per_cell": STEP_BYTES_PER_CELL_16}
             vs.close()
 
+    if variants is None:
+        solver.close()
+
+    serving = None
+    if not args.no_serving:
+        barrier()
+        serving = run_serving(args, rank)
+        barrier()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline()
@@ -415,12 +478,11 @@ def run_ours(args):
                 "kernels": kernels,
                 "tuning": {k: v["value"] for k, v in tuning.items()} if tuning else None,
                 "storage_variants": variants,
+                "serving": serving,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
                 "gpu_launches": 3 * args.steps,
                 "sum_phi": sum_phi}
         print(json.dumps(line), flush=True)
-    if variants is None:
-        solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -441,6 +503,16 @@ def main(argv=None):
                     help="skip timing the FP16/BF16 population-storage variants")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the untimed autotuning of prefetch distances")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the request-loop leg (batched vs one at a time)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-scale", type=float, default=0.1,
+                    help="step counts are uniform in [2000, 20000] times this")
+    ap.add_argument("--serve-load", type=float, default=1.5,
+                    help="offered load in units of the one-at-a-time capacity")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-quantum", type=int, default=64)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -168,6 +168,14 @@ lbm_status lbm_read_fields(lbm_ctx* ctx, unsigned mask, double* phi, double* rho
  * momentum value is not finite.  Synchronises the stream. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double* sum_phi, double mom[3]);
 
+/* The same sums without waiting: enqueued on the context's stream, they land in
+ * out_dev[0..4] = {sum phi, momentum x, y, z, number of cells with a non-finite phi or
+ * momentum}.  out_dev: 5 doubles, 8-byte aligned, device memory (or host memory the
+ * device can write), owned by the caller; valid once the stream has passed this
+ * point.  Lets a scheduler watch many runs for divergence without a synchronisation
+ * per run.  LBM_EINVAL for NULL or misaligned out_dev or an uninitialised context. */
+lbm_status lbm_reduce_async(lbm_ctx* ctx, double* out_dev);
+
 /* Full state in the paper's velocity order (Eqs. 6 and 23): the populations at the
  * current time just after propagation, f (7N) and g (15N), planar by population, and
  * the phi u of the previous step (3N, planar; all zero while no step has been taken
@@ -221,8 +229,54 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms,
 lbm_status lbm_field_sum_noalloc(const float* field, long long n, double* out,
                                  void* cuda_stream);
 
+/* Device bytes lbm_create would allocate for `grid` and `params` (same checks as
+ * lbm_create); lets a scheduler admit runs against a memory budget. */
+lbm_status lbm_memory_bytes(const lbm_grid* grid, const lbm_params* params, size_t* bytes);
+
 /* Release all device memory of the context and the context itself. */
 lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Batches: many runs advanced together.  The paper has no counterpart; this serves
+ * many simulations on one GPU.  lbm_batch_step(b, runs, n, steps) advances every run
+ * by `steps` time steps with one launch per pass per time step for all of them: a
+ * persistent grid strides over (run, block) work items read from a device table, and
+ * the launches of a batch step are a CUDA graph instantiated once per (steps, grid
+ * sizes, storage type) and replayed for any run set.  Results are those of lbm_step on
+ * each run alone (same per-cell code).  Runs need LBM_PATTERN_AB, the coupled model
+ * (no prescribed velocity), no LBM_FLAG_SRT_FLOW / LBM_FLAG_D3Q7_STENCIL, one storage
+ * type per batch, at most 256 per call, and at least one step taken since lbm_init_phi
+ * (the first step, with d_t(phi u) = 0, goes through lbm_step); LBM_EINVAL otherwise.
+ * Every run advances by exactly `steps`.  The batch's stream waits for each run's stream
+ * and each run's stream then waits for the batch, so batched and single steps mix
+ * safely; with cuda_stream NULL the batch uses a stream of its own (graph capture needs
+ * one).  A run must not be destroyed before its stream has passed the batch step.
+ * Schedule: each pass's work items (blocks of 256 cells; bricks for pass 1) are taken
+ * by a persistent grid that strides over them, or by one block per item.
+ * lbm_batch_set_grid sets the blocks of pass 0 (order parameter), 1 (chemical
+ * potential) or 2 (stream-collide): 1..2^24 persistent blocks, 0 one block per item;
+ * defaults 8 and 6 persistent blocks per SM for passes 0 and 1, one block per item for
+ * pass 2.  lbm_batch_set_prefetch sets how many items ahead passes 0
+ * and 2 prefetch into L2: -1 (default) one wave (the persistent grid, else SMs x
+ * resident blocks), 0 off.  lbm_batch_set_split(b, cells): runs of at least `cells`
+ * cells are stepped by lbm_step on their own streams instead (they fill the GPU alone,
+ * and the single-run kernels take their parameters from the constant bank); the other
+ * runs share the batched launches on the batch's stream, and the two overlap.  0
+ * (default) sends every run through the shared launches.  Errors:
+ * LBM_EINVAL for a refused call (nothing is launched and no run changes), LBM_ECUDA
+ * for a failed capture or launch; lbm_batch_last_error says why.
+ * --------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(const lbm_allocator* alloc, void* cuda_stream, lbm_batch** out);
+lbm_status lbm_batch_step(lbm_batch* b, lbm_ctx* const* runs, int nruns, int steps);
+lbm_status lbm_batch_set_grid(lbm_batch* b, int pass, int blocks);
+lbm_status lbm_batch_get_grid(const lbm_batch* b, int pass, int* blocks);
+lbm_status lbm_batch_set_split(lbm_batch* b, long long cells);
+lbm_status lbm_batch_get_split(const lbm_batch* b, long long* cells);
+lbm_status lbm_batch_set_prefetch(lbm_batch* b, int pass, int items);
+lbm_status lbm_batch_get_prefetch(const lbm_batch* b, int pass, int* items);
+lbm_status lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* Message of the last failure on ctx ("" if none); for ctx == NULL, the message of the
  * last lbm_create failure in this process. */

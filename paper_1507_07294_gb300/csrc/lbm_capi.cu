@@ -3,6 +3,8 @@
 // time step.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +13,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_capi_internal.h"
 #include "lbm_internal.h"
 
 struct lbm_ctx {
@@ -211,6 +214,43 @@ lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, std::vector
 
 void lbm::set_global_error(const std::string& msg) { g_create_error = msg; }
 
+int lbm::ctx_storage(const lbm_ctx* c) { return c->geo.storage; }
+
+bool lbm::ctx_batchable(const lbm_ctx* c, std::string* why) {
+  const char* r = nullptr;
+  if (!c->initialized)
+    r = "not initialised";
+  else if (c->params.pattern != LBM_PATTERN_AB)
+    r = "batches need LBM_PATTERN_AB";
+  else if (c->vel_kind != LBM_VELOCITY_NONE)
+    r = "batches run the coupled model only";
+  else if (c->params.flags & (LBM_FLAG_SRT_FLOW | LBM_FLAG_D3Q7_STENCIL))
+    r = "batches run the default model variant only";
+  if (r && why) *why = r;
+  return r == nullptr;
+}
+
+bool lbm::ctx_have_prev(const lbm_ctx* c) { return c->have_prev; }
+
+cudaStream_t lbm::ctx_stream(const lbm_ctx* c) { return c->stream; }
+
+void lbm::ctx_describe(const lbm_ctx* c, lbm::Geometry* geo, lbm::Physics* ph, float** state0,
+                       float** state1, float** phi, float** mu, int* parity) {
+  *geo = c->geo;
+  *ph = c->ph;
+  *state0 = c->pop[0];
+  *state1 = c->pop[1];
+  *phi = c->phi;
+  *mu = c->mu;
+  *parity = c->cur;
+}
+
+void lbm::ctx_advance(lbm_ctx* c, int n) {
+  c->cur = (c->cur + n) & 1;
+  c->step += n;
+  c->have_prev = true;
+}
+
 extern "C" {
 
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_allocator* alloc,
@@ -395,6 +435,18 @@ lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
   return LBM_OK;
 }
 
+lbm_status lbm_reduce_async(lbm_ctx* c, double* out_dev) {
+  if (!c) return LBM_EINVAL;
+  if (!out_dev || reinterpret_cast<uintptr_t>(out_dev) % alignof(double) != 0)
+    return fail(c, LBM_EINVAL, "out_dev must be a non-NULL, 8-byte aligned pointer");
+  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  float* phi_now = c->stage + 5 * c->geo.stride;
+  LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, phi_now, c->geo, read_pattern(c), c->stream));
+  LBM_CK(c, lbm::launch_reduce(cur_state(c), phi_now, c->partial, out_dev, c->geo,
+                               read_pattern(c), c->vel_kind == LBM_VELOCITY_NONE, c->stream));
+  return LBM_OK;
+}
+
 lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long long* step) {
   if (!c) return LBM_EINVAL;
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
@@ -518,6 +570,18 @@ lbm_status lbm_profile_read(lbm_ctx* c, int kernel, double* total_ms, long long*
   }
   *total_ms = total;
   *launches = static_cast<long long>(c->events[kernel].size());
+  return LBM_OK;
+}
+
+lbm_status lbm_memory_bytes(const lbm_grid* grid, const lbm_params* params, size_t* bytes) {
+  if (!bytes) return fail(nullptr, LBM_EINVAL, "bytes must not be NULL");
+  const lbm_status st = validate(grid, params);
+  if (st != LBM_OK) return st;
+  const long long n = static_cast<long long>(grid->nx) * grid->ny * grid->nz;
+  const size_t plane = static_cast<size_t>((n + 63) / 64 * 64) * sizeof(float);
+  const size_t state = lbm::state_bytes(static_cast<int>(n), params->storage);
+  *bytes = state * (params->pattern == LBM_PATTERN_AB ? 2 : 1) + plane * 9 +
+           sizeof(double) * (5 * lbm::kReduceMaxParts + 8);
   return LBM_OK;
 }
 

@@ -1,0 +1,212 @@
+// Per-cell and per-brick bodies of the three step passes, shared by the single-run
+// kernels (lbm_kernels.cu) and the batched kernels that advance many runs in one launch
+// (lbm_batch.cu).  See lbm_kernels.cu for what each pass computes.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kBlock = 256;
+
+// Resident blocks per SM the stream-collide kernels are compiled for (80 registers).
+#ifndef LBM_COLLIDE_MIN_BLOCKS
+#define LBM_COLLIDE_MIN_BLOCKS 3
+#endif
+
+// Bulk prefetch of [p, p + bytes) into L2 (a hint: no completion to wait for).  p must be
+// 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch, by the calling thread, of what a block streams for the kBlock cells that
+// start at cell `first` (a multiple of kBlock): with ALL_SLOTS the whole cell state (all
+// 25 slots) and phi and mu of those cells, else the 7 f slots of each tile.  Ranges are
+// clipped to the arrays.
+template <int S, bool ALL_SLOTS>
+__device__ __forceinline__ void prefetch_cells(const float* state, const float* phi,
+                                               const float* mu, const Geometry& geo,
+                                               long long first) {
+  if (first < 0 || first >= geo.n) return;
+  const long long cells = min(static_cast<long long>(kBlock), geo.n - first);
+  // kBlock is a multiple of kTile, so `first` starts a tile
+  const int tiles = static_cast<int>((cells + kTile - 1) / kTile);
+  const float* t0 = state + tile_floats<S>(static_cast<int>(first));
+  if (ALL_SLOTS) {
+    prefetch_l2(t0, static_cast<unsigned>(tiles * tile_bytes<S>()));
+    const unsigned bytes = static_cast<unsigned>(cells * sizeof(float)) & ~15u;
+    if (bytes) {
+      prefetch_l2(phi + first, bytes);
+      prefetch_l2(mu + first, bytes);
+    }
+  } else {
+    for (int t = 0; t < tiles; ++t)
+      prefetch_l2(t0 + t * (tile_bytes<S>() / 4),
+                  static_cast<unsigned>(kQ7 * kTile * sizeof(typename Elem<S>::T)));
+  }
+}
+
+__device__ __forceinline__ void cell_coords(const Geometry& geo, int idx, int& x, int& y, int& z) {
+  const int r = fast_div(idx, geo.div_nx);
+  x = idx - r * geo.nx;
+  z = fast_div(r, geo.div_ny);
+  y = r - z * geo.ny;
+}
+
+
+// ---------------------------------------------------------- order parameter -------
+// phi = sum_i f_i of the streamed populations (Eqs. 13, 16).  With 16-bit storage slot
+// 0 holds f_0 - phi_ref, phi_ref the order parameter of the step that wrote it;
+// phi_ref and phi may be the same array (each thread reads its own cell first).
+template <int P, int S>
+__device__ __forceinline__ void phi_cell(const float* src, const float* phi_ref, float* phi,
+                                         const Geometry& geo, int idx) {
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
+  float f[7];
+  load_f<P, S>(src, idx, nb, f);
+  if (S != kF32) f[0] += phi_ref[idx];
+  phi[idx] = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]));
+}
+
+// ------------------------------------------------------- chemical potential -------
+// Shared-memory tiling of the 15-point stencil: a block of kTX x kTY threads computes a
+// kTX x kTY x kTZ brick of cells from one load of the brick plus a one-cell halo, so
+// each phi value is read from global memory (kTX+2)(kTY+2)(kTZ+2)/(kTX kTY kTZ) = 1.5
+// times instead of 15 times.  The halo is loaded row by row (one address computation
+// per row of kTX + 2 values), and each thread walks its column in z keeping, per plane,
+// the centre, the sum of the 4 in-plane face neighbours and the sum of the 4 in-plane
+// diagonal neighbours, so every plane is summed once for the three cells that use it.
+constexpr int kTX = 32, kTY = 8, kTZ = 16;
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;
+
+// v mod n for v in [-1, n + span): a compare and add when n >= span, else a modulo.
+__device__ __forceinline__ int wrap(int v, int n, int span) {
+  if (n >= span) return v < 0 ? v + n : (v >= n ? v - n : v);
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2) for brick (bx, by, bz) of the grid;
+// called by all kTX x kTY threads of a block, `tile` in shared memory.  The only barrier
+// is the one after the tile load; threads outside the grid return after it, so a caller
+// that reuses `tile` for another brick must synchronise the block first.
+template <bool D3Q7>
+__device__ __forceinline__ void mu_brick(const float* __restrict__ phi, float* __restrict__ mu,
+                                         const Geometry& geo, const Physics& ph, int bx, int by,
+                                         int bz, float (*tile)[kHY][kHX]) {
+  const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  // columns of the halo brick this lane loads: j = lane and, for lanes 0-1, j = 32 + lane
+  const int gx_a = wrap(x0 - 1 + lane, geo.nx, kHX);
+  const int gx_b = wrap(x0 - 1 + kTX + (lane & 1), geo.nx, kHX);
+  for (int r = warp; r < kHZ * kHY; r += kTY) {
+    const int l = r / kHY, i = r - l * kHY;
+    const int gy = wrap(y0 - 1 + i, geo.ny, kHY);
+    const int zz = z0 - 1 + l;
+    const int gz = geo.walls ? min(max(zz, 0), geo.nz - 1) : wrap(zz, geo.nz, kHZ);
+    const float* row = phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx;
+    tile[l][i][lane] = __ldg(row + gx_a);
+    if (lane < 2) tile[l][i][kTX + lane] = __ldg(row + gx_b);
+  }
+  __syncthreads();
+  const int x = x0 + lane, y = y0 + warp;
+  if (x >= geo.nx || y >= geo.ny) return;  // no barrier follows in this function
+  const int i = warp + 1, j = lane + 1;
+  // per-plane partial sums of column (i, j): centre, faces, diagonals
+  auto plane = [&](int l, float& c, float& f, float& d) {
+    c = tile[l][i][j];
+    f = (tile[l][i][j - 1] + tile[l][i][j + 1]) + (tile[l][i - 1][j] + tile[l][i + 1][j]);
+    d = (tile[l][i - 1][j - 1] + tile[l][i - 1][j + 1]) + (tile[l][i + 1][j - 1] + tile[l][i + 1][j + 1]);
+  };
+  float c0, f0, d0, c1, f1, d1;
+  plane(0, c0, f0, d0);
+  plane(1, c1, f1, d1);
+  const int nl = min(kTZ, geo.nz - z0);
+  float* out = mu + (static_cast<size_t>(z0) * geo.ny + y) * geo.nx + x;
+  const size_t zstride = static_cast<size_t>(geo.plane);
+  for (int l = 1; l <= nl; ++l) {
+    float c2, f2, d2;
+    plane(l + 1, c2, f2, d2);
+    // Eq. 36 on the D3Q15 stencil: 2/3 (faces - 6 c) + 1/12 (corners - 8 c); with the
+    // D3Q7 weights: faces - 6 c
+    const float lap = D3Q7 ? (f1 + (c0 + c2)) - 6.0f * c1
+                           : (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
+                                 (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
+    out[(l - 1) * zstride] = chemical_potential(ph, c1, lap);
+    c0 = c1; f0 = f1; d0 = d1;
+    c1 = c2; f1 = f2; d1 = d2;
+  }
+}
+
+// ------------------------------------------------------ fused stream-collide -------
+// Stencil quantities of one cell: grad phi (Eq. 35), lap mu (Eq. 36), centre values.
+struct CellStencils {
+  float grad_phi[3], lap_mu, phi, mu;
+};
+
+template <bool D3Q7 = false>
+__device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ phi,
+                                                      const float* __restrict__ mu, int idx,
+                                                      const Nbr& nb) {
+  CellStencils cs;
+  {
+    Stencil s;
+    load_stencil(phi, idx, nb, s);
+    if (D3Q7)
+      stencil_grad7(s, cs.grad_phi);
+    else
+      stencil_grad(s, cs.grad_phi);
+    cs.phi = s.c;
+  }
+  {
+    Stencil s;
+    load_stencil(mu, idx, nb, s);
+    cs.lap_mu = D3Q7 ? stencil_lap7(s) : stencil_lap(s);
+    cs.mu = s.c;
+  }
+  return cs;
+}
+
+
+// Pull f and g, stencils of phi and mu, forces, u and p, both MRT collisions,
+// d_t(phi u), store f+ and g+ (Eqs. 14-34).  src and dst are the same array for the
+// in-place patterns.  All 25 cell-state loads are issued first so that they are in
+// flight together with the stencil loads.
+template <int P, int VAR, int S>
+__device__ __forceinline__ void collide_cell(const float* src, float* dst,
+                                             const float* __restrict__ phi,
+                                             const float* __restrict__ mu, const Geometry& geo,
+                                             const Physics& ph, int have_prev, int idx) {
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
+
+  float g[15], f[7], prev[3];
+  load_g<P, S>(src, idx, nb, g);
+  load_f<P, S>(src, idx, nb, f);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
+
+  const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
+  const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
+  const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
+  collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
+  store_g<P, S>(dst, idx, nb, g);
+
+  // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
+  float dphiu[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float cur = cs.phi * M.u[a];
+    dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
+    dst[phiu_index<S>(idx, a)] = cur;
+  }
+
+  collide_d3q7<S != kF32>(ph, f, cs.phi, cs.mu, M.u, dphiu);
+  store_f<P, S>(dst, idx, nb, f);
+}
+
+}  // namespace lbm

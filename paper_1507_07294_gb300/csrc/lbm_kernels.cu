@@ -11,6 +11,7 @@
 // Every kernel is templated on the population storage pattern (lbm_device.cuh).
 #include <cuda_runtime.h>
 
+#include "lbm_cells.cuh"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -18,48 +19,17 @@ namespace lbm {
 
 namespace {
 
-constexpr int kBlock = 256;
-
-__device__ __forceinline__ void cell_coords(const Geometry& geo, int idx, int& x, int& y, int& z) {
-  const int r = fast_div(idx, geo.div_nx);
-  x = idx - r * geo.nx;
-  z = fast_div(r, geo.div_ny);
-  y = r - z * geo.ny;
-}
-
-// Bulk prefetch of [p, p + bytes) into L2 (a hint: no completion to wait for).  p must be
-// 16-byte aligned and bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // Latency hiding for the streaming kernels: thread 0 of block b prefetches into L2 the
 // data of the cells of block b + dist, which a block of the next wave will stream in
 // (dist = one wave: SMs x resident blocks per SM).  k_collide prefetches the whole cell
 // state of those cells (all 25 slots) and their phi and mu; k_phi only the 7 f slots of
-// each tile.  All ranges are clipped to the arrays.
+// each tile.
 template <int S, bool ALL_SLOTS>
 __device__ __forceinline__ void prefetch_ahead(const float* state, const float* phi, const float* mu,
                                                const Geometry& geo, int dist) {
   if (dist <= 0 || threadIdx.x != 0) return;
-  const long long first = static_cast<long long>(blockIdx.x + dist) * kBlock;
-  if (first >= geo.n) return;
-  const long long cells = min(static_cast<long long>(kBlock), geo.n - first);
-  // kBlock is a multiple of kTile, so `first` starts a tile
-  const int tiles = static_cast<int>((cells + kTile - 1) / kTile);
-  const float* t0 = state + tile_floats<S>(static_cast<int>(first));
-  if (ALL_SLOTS) {
-    prefetch_l2(t0, static_cast<unsigned>(tiles * tile_bytes<S>()));
-    const unsigned bytes = static_cast<unsigned>(cells * sizeof(float)) & ~15u;
-    if (bytes) {
-      prefetch_l2(phi + first, bytes);
-      prefetch_l2(mu + first, bytes);
-    }
-  } else {
-    for (int t = 0; t < tiles; ++t)
-      prefetch_l2(t0 + t * (tile_bytes<S>() / 4),
-                  static_cast<unsigned>(kQ7 * kTile * sizeof(typename Elem<S>::T)));
-  }
+  prefetch_cells<S, ALL_SLOTS>(state, phi, mu, geo,
+                               static_cast<long long>(blockIdx.x + dist) * kBlock);
 }
 
 // ------------------------------------------------------------------ k_phi ---------
@@ -72,116 +42,19 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
   prefetch_ahead<S, false>(src, nullptr, nullptr, geo, geo.prefetch_phi);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
-  int x, y, z;
-  cell_coords(geo, idx, x, y, z);
-  const Nbr nb = make_nbr(geo, x, y, z);
-  float f[7];
-  load_f<P, S>(src, idx, nb, f);
-  if (S != kF32) f[0] += phi_ref[idx];
-  phi[idx] = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]));
+  phi_cell<P, S>(src, phi_ref, phi, geo, idx);
 }
 
 // ------------------------------------------------------------------- k_mu ---------
-// Shared-memory tiling of the 15-point stencil: a block of kTX x kTY threads computes a
-// kTX x kTY x kTZ brick of cells from one load of the brick plus a one-cell halo, so
-// each phi value is read from global memory (kTX+2)(kTY+2)(kTZ+2)/(kTX kTY kTZ) = 1.5
-// times instead of 15 times.  The halo is loaded row by row (one address computation
-// per row of kTX + 2 values), and each thread walks its column in z keeping, per plane,
-// the centre, the sum of the 4 in-plane face neighbours and the sum of the 4 in-plane
-// diagonal neighbours, so every plane is summed once for the three cells that use it.
-constexpr int kTX = 32, kTY = 8, kTZ = 16;
-constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;
-
-// v mod n for v in [-1, n + span): a compare and add when n >= span, else a modulo.
-__device__ __forceinline__ int wrap(int v, int n, int span) {
-  if (n >= span) return v < 0 ? v + n : (v >= n ? v - n : v);
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
 template <bool D3Q7>
 __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
                                                  float* __restrict__ mu, Geometry geo,
                                                  Physics ph) {
   __shared__ float tile[kHZ][kHY][kHX];
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
-  const int lane = threadIdx.x, warp = threadIdx.y;
-  // columns of the halo brick this lane loads: j = lane and, for lanes 0-1, j = 32 + lane
-  const int gx_a = wrap(x0 - 1 + lane, geo.nx, kHX);
-  const int gx_b = wrap(x0 - 1 + kTX + (lane & 1), geo.nx, kHX);
-  for (int r = warp; r < kHZ * kHY; r += kTY) {
-    const int l = r / kHY, i = r - l * kHY;
-    const int gy = wrap(y0 - 1 + i, geo.ny, kHY);
-    const int zz = z0 - 1 + l;
-    const int gz = geo.walls ? min(max(zz, 0), geo.nz - 1) : wrap(zz, geo.nz, kHZ);
-    const float* row = phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx;
-    tile[l][i][lane] = __ldg(row + gx_a);
-    if (lane < 2) tile[l][i][kTX + lane] = __ldg(row + gx_b);
-  }
-  __syncthreads();
-  const int x = x0 + lane, y = y0 + warp;
-  if (x >= geo.nx || y >= geo.ny) return;
-  const int i = warp + 1, j = lane + 1;
-  // per-plane partial sums of column (i, j): centre, faces, diagonals
-  auto plane = [&](int l, float& c, float& f, float& d) {
-    c = tile[l][i][j];
-    f = (tile[l][i][j - 1] + tile[l][i][j + 1]) + (tile[l][i - 1][j] + tile[l][i + 1][j]);
-    d = (tile[l][i - 1][j - 1] + tile[l][i - 1][j + 1]) + (tile[l][i + 1][j - 1] + tile[l][i + 1][j + 1]);
-  };
-  float c0, f0, d0, c1, f1, d1;
-  plane(0, c0, f0, d0);
-  plane(1, c1, f1, d1);
-  const int nl = min(kTZ, geo.nz - z0);
-  float* out = mu + (static_cast<size_t>(z0) * geo.ny + y) * geo.nx + x;
-  const size_t zstride = static_cast<size_t>(geo.plane);
-  for (int l = 1; l <= nl; ++l) {
-    float c2, f2, d2;
-    plane(l + 1, c2, f2, d2);
-    // Eq. 36 on the D3Q15 stencil: 2/3 (faces - 6 c) + 1/12 (corners - 8 c); with the
-    // D3Q7 weights: faces - 6 c
-    const float lap = D3Q7 ? (f1 + (c0 + c2)) - 6.0f * c1
-                           : (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
-                                 (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
-    out[(l - 1) * zstride] = chemical_potential(ph, c1, lap);
-    c0 = c1; f0 = f1; d0 = d1;
-    c1 = c2; f1 = f2; d1 = d2;
-  }
-}
-
-// Stencil quantities of one cell: grad phi (Eq. 35), lap mu (Eq. 36), centre values.
-struct CellStencils {
-  float grad_phi[3], lap_mu, phi, mu;
-};
-
-template <bool D3Q7 = false>
-__device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ phi,
-                                                      const float* __restrict__ mu, int idx,
-                                                      const Nbr& nb) {
-  CellStencils cs;
-  {
-    Stencil s;
-    load_stencil(phi, idx, nb, s);
-    if (D3Q7)
-      stencil_grad7(s, cs.grad_phi);
-    else
-      stencil_grad(s, cs.grad_phi);
-    cs.phi = s.c;
-  }
-  {
-    Stencil s;
-    load_stencil(mu, idx, nb, s);
-    cs.lap_mu = D3Q7 ? stencil_lap7(s) : stencil_lap(s);
-    cs.mu = s.c;
-  }
-  return cs;
+  mu_brick<D3Q7>(phi, mu, geo, ph, blockIdx.x, blockIdx.y, blockIdx.z, tile);
 }
 
 // -------------------------------------------------------------- k_collide ---------
-// src and dst are the same array for the in-place patterns.  All 25 cell-state loads
-// are issued first so that they are in flight together with the stencil loads.
-#ifndef LBM_COLLIDE_MIN_BLOCKS
-#define LBM_COLLIDE_MIN_BLOCKS 3
-#endif
 
 template <int P, int VAR, int S>
 __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
@@ -190,33 +63,7 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if (idx >= geo.n) return;
-  int x, y, z;
-  cell_coords(geo, idx, x, y, z);
-  const Nbr nb = make_nbr(geo, x, y, z);
-
-  float g[15], f[7], prev[3];
-  load_g<P, S>(src, idx, nb, g);
-  load_f<P, S>(src, idx, nb, f);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
-
-  const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
-  const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
-  const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
-  collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
-  store_g<P, S>(dst, idx, nb, g);
-
-  // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
-  float dphiu[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float cur = cs.phi * M.u[a];
-    dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
-    dst[phiu_index<S>(idx, a)] = cur;
-  }
-
-  collide_d3q7<S != kF32>(ph, f, cs.phi, cs.mu, M.u, dphiu);
-  store_f<P, S>(dst, idx, nb, f);
+  collide_cell<P, VAR, S>(src, dst, phi, mu, geo, ph, have_prev, idx);
 }
 
 // ------------------------------------------------------------------ k_che ---------

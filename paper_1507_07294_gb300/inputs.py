@@ -104,25 +104,32 @@ def droplet(n: int = 32, R: float = 8.0, D: float = 4.0, sigma: float = 0.01,
 def rayleigh_taylor(W: int = 64, Re: float = 256.0, atwood: float = 0.5,
                     sqrt_gW: float = 0.04, D: float = 4.0, sigma: float = 1e-4,
                     Pe: float = 50.0, rho_g: float = 1.0, steps: int = 20000,
-                    nz: Optional[int] = None) -> Workload:
+                    nz: Optional[int] = None, with_fields: bool = True) -> Workload:
     """Rayleigh-Taylor box W x W x 4W: heavy fluid (phi = +1) above z = 2W + h(x, y).
 
     Eq. 42 gives h, Eq. 43 phi0 and Eq. 44 Re = sqrt(gW) W / nu; the mobility follows
-    from Pe = sqrt(gW) W / Mob.  Lateral boundaries periodic, z walled.
+    from Pe = sqrt(gW) W / Mob.  Lateral boundaries periodic, z walled.  With
+    with_fields False phi0 is left None (it depends on W, nz and D only; callers that
+    make many runs of one grid build it once with rt_interface).
     """
     nz = 4 * W if nz is None else nz
     rho_l = rho_g * (1.0 + atwood) / (1.0 - atwood)
     gacc = sqrt_gW ** 2 / W
     nu = sqrt_gW * W / Re
     mob = sqrt_gW * W / Pe
-    x, y, z = node_coords(W, W, nz, True)
-    h = 0.05 * W * (np.cos(2 * math.pi * x / W) + np.cos(2 * math.pi * y / W))
-    phi0 = np.tanh(2.0 * (z - h - nz / 2.0) / D)
-    phi0 = np.broadcast_to(phi0, (nz, W, W)).copy()
+    phi0 = rt_interface(W, nz, D) if with_fields else None
     return Workload(name=f"rt{W}x{W}x{nz}_Re{Re:g}", nx=W, ny=W, nz=nz, walls_z=True,
                     rho_l=rho_l, rho_g=rho_g, nu_l=nu, nu_g=nu, mobility=mob, D=D,
                     sigma=sigma, g=(0.0, 0.0, -gacc), sf=SF_COUPLED, steps=steps,
                     U=sqrt_gW, phi0=phi0)
+
+
+def rt_interface(W: int, nz: int, D: float = 4.0) -> np.ndarray:
+    """phi0 of Eq. 43 around the perturbed plane z = nz/2 + h(x, y) of Eq. 42."""
+    x, y, z = node_coords(W, W, nz, True)
+    h = 0.05 * W * (np.cos(2 * math.pi * x / W) + np.cos(2 * math.pi * y / W))
+    phi0 = np.tanh(2.0 * (z - h - nz / 2.0) / D)
+    return np.broadcast_to(phi0, (nz, W, W)).copy()
 
 
 def flat_interface(nz: int = 32, nxy: int = 4, D: float = 4.0, sigma: float = 0.01,

@@ -87,6 +87,18 @@ _SIGNATURES = {
     "lbm_profile": (c_int, [c_void_p, c_int]),
     "lbm_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_longlong)]),
     "lbm_field_sum_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_void_p]),
+    "lbm_memory_bytes": (c_int, [POINTER(LbmGrid), POINTER(LbmParams), POINTER(c_size_t)]),
+    "lbm_batch_create": (c_int, [POINTER(LbmAllocator), c_void_p, POINTER(c_void_p)]),
+    "lbm_batch_step": (c_int, [c_void_p, POINTER(c_void_p), c_int, c_int]),
+    "lbm_batch_set_grid": (c_int, [c_void_p, c_int, c_int]),
+    "lbm_reduce_async": (c_int, [c_void_p, c_void_p]),
+    "lbm_batch_get_grid": (c_int, [c_void_p, c_int, POINTER(c_int)]),
+    "lbm_batch_set_prefetch": (c_int, [c_void_p, c_int, c_int]),
+    "lbm_batch_set_split": (c_int, [c_void_p, c_longlong]),
+    "lbm_batch_get_split": (c_int, [c_void_p, POINTER(c_longlong)]),
+    "lbm_batch_get_prefetch": (c_int, [c_void_p, c_int, POINTER(c_int)]),
+    "lbm_batch_destroy": (c_int, [c_void_p]),
+    "lbm_batch_last_error": (c_char_p, [c_void_p]),
     "lbm_destroy": (c_int, [c_void_p]),
     "lbm_last_error": (c_char_p, [c_void_p]),
 }
@@ -256,6 +268,13 @@ def lbm_reduce(ctx: Context, check: bool = True):
     return s.value, np.array(mom[:]), st
 
 
+def lbm_reduce_async(ctx: Context, out_dev: int) -> None:
+    """Enqueues the FP64 sums into 5 doubles at device address out_dev: sum phi,
+    momentum x, y, z, count of non-finite cells.  No synchronisation."""
+    lib = load_library()
+    _check(lib, lib.lbm_reduce_async(ctx.handle, c_void_p(out_dev)), ctx.handle)
+
+
 def lbm_read_state(ctx: Context):
     """Returns (f[7, z, y, x], g[15, z, y, x], phiu_prev[3, z, y, x], step), float32."""
     lib = load_library()
@@ -328,6 +347,85 @@ def lbm_field_sum_noalloc(field_ptr: int, n: int, out_ptr: int, stream: Optional
         stream = torch.cuda.current_stream().cuda_stream
     _check(lib, lib.lbm_field_sum_noalloc(c_void_p(field_ptr), int(n), c_void_p(out_ptr),
                                           c_void_p(stream)), None)
+
+
+def lbm_memory_bytes(grid: LbmGrid, params: LbmParams) -> int:
+    """Device bytes lbm_create would allocate (no GPU needed)."""
+    lib = load_library()
+    out = c_size_t()
+    _check(lib, lib.lbm_memory_bytes(ctypes.byref(grid), ctypes.byref(params), ctypes.byref(out)),
+           None)
+    return out.value
+
+
+class Batch:
+    """lbm_batch: advances many contexts together (one launch per pass for all)."""
+
+    def __init__(self, stream: Optional[int] = None, allocator: str = "torch"):
+        lib = load_library()
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._alloc = _TorchAllocator(stream) if allocator == "torch" else None
+        out = c_void_p()
+        st = lib.lbm_batch_create(ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                  c_void_p(stream), ctypes.byref(out))
+        _check(lib, st, None)
+        self.handle = out
+        self.lib = lib
+
+    def _check(self, st):
+        if st != LBM_OK:
+            msg = self.lib.lbm_batch_last_error(self.handle)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    def step(self, contexts, steps: int) -> None:
+        """lbm_batch_step over the given Contexts (or Solvers)."""
+        handles = [(c.ctx if hasattr(c, "ctx") else c).handle.value for c in contexts]
+        arr = (c_void_p * len(handles))(*handles)
+        self._check(self.lib.lbm_batch_step(self.handle, arr, len(handles), int(steps)))
+
+    def set_grid(self, pass_index: int, blocks: int) -> None:
+        self._check(self.lib.lbm_batch_set_grid(self.handle, int(pass_index), int(blocks)))
+
+    def get_grid(self, pass_index: int) -> int:
+        v = c_int()
+        self._check(self.lib.lbm_batch_get_grid(self.handle, int(pass_index), ctypes.byref(v)))
+        return v.value
+
+    def set_split(self, cells: int) -> None:
+        """Runs of at least `cells` cells take their own launches (0: none do)."""
+        self._check(self.lib.lbm_batch_set_split(self.handle, int(cells)))
+
+    def get_split(self) -> int:
+        v = c_longlong()
+        self._check(self.lib.lbm_batch_get_split(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def set_prefetch(self, pass_index: int, items: int) -> None:
+        self._check(self.lib.lbm_batch_set_prefetch(self.handle, int(pass_index), int(items)))
+
+    def get_prefetch(self, pass_index: int) -> int:
+        v = c_int()
+        self._check(self.lib.lbm_batch_get_prefetch(self.handle, int(pass_index), ctypes.byref(v)))
+        return v.value
+
+    def close(self) -> None:
+        if self.handle is not None and self.handle.value is not None:
+            self.lib.lbm_batch_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lbm_destroy(ctx: Context) -> None:
