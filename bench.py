@@ -56,11 +56,12 @@ STEP_BYTES_PER_CELL_16 = COLLIDE_BYTES_PER_CELL_16 + (7 * 2 + 4 + 4) + 8
 
 # DRAM traffic of k_collide per cell from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the cells of the captured launch), valid only for
-# the kernel source it was taken on (hash of csrc/lbm_device.cuh + lbm_kernels.cu).
+# the kernel source it was taken on (hash of csrc/lbm_device.cuh, lbm_cells.cuh and
+# lbm_kernels.cu).
 NCU_TRAFFIC = {
-    # profiles/step_kernels_rt128x128x512_full.md: 1704.6 MB per launch over 8,388,608
+    # profiles/step_kernels_rt128x128x512_full.md: 1705.0 MB per launch over 8,388,608
     # cells (ncu --set full on the 128x128x512 case, scaled by cells to the benchmark)
-    "k_collide": {"bytes_per_cell": 203.20, "kernel_sha": "9d8d70f12cd50971"},
+    "k_collide": {"bytes_per_cell": 203.25, "kernel_sha": "1184771e0eac09d0"},
 }
 
 WORKLOADS = {
@@ -73,7 +74,7 @@ WORKLOADS = {
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("lbm_device.cuh", "lbm_kernels.cu"):
+    for name in ("lbm_device.cuh", "lbm_cells.cuh", "lbm_kernels.cu"):
         with open(os.path.join(ROOT, "paper_1507_07294_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
