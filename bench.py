@@ -10,8 +10,9 @@ Printed JSON line (rank 0):
   value      MLUPS (million cell updates per second) over all ranks, device-timed with
              CUDA events around exactly --steps steps; inputs resident in HBM.
   e2e        the same metric through the public C ABI with host buffers: pinned-host
-             phi0 uploaded by lbm_init_phi, every step followed by lbm_reduce (FP64 mass
-             and momentum, read back to the host), lbm_read_fields (phi, u, p) at the end.
+             phi0 uploaded by lbm_init_phi, every step taken by lbm_step_reduce (the step
+             plus the FP64 mass and momentum of its result, read back to the host),
+             lbm_read_fields (phi, u, p) at the end.
   roofline   the fused stream-collide kernel: algorithmic bytes per launch / its mean
              CUDA-event duration, against the measured HBM copy bandwidth.
   cpu_baseline  the FP64 oracle, single-threaded, on a bounded sample (rank 0, N = 1).
@@ -402,19 +403,21 @@ def run_ours(args):
     if not args.no_e2e:
         phi_host = torch.empty(cells, dtype=torch.float64, pin_memory=True).numpy()
         phi_host[:] = w.phi0.reshape(-1)
+        # page-locked result buffers, allocated once like a server's I/O buffers
+        outs = {k: torch.empty(c * cells, dtype=torch.float64, pin_memory=True).numpy()
+                for k, c in (("phi", 1), ("u", 3), ("p", 1))}
         barrier()
         t0 = time.perf_counter()
         L.lbm_init_phi(ctx, phi_host)
         for _ in range(args.steps):
-            L.lbm_step(ctx, 1)
-            L.lbm_reduce(ctx)
-        out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P)
+            L.lbm_step_reduce(ctx, 1)  # the step and the FP64 sums of its result
+        out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P, out=outs)
         barrier()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         assert np.isfinite(out["phi"]).all()
         e2e = {"value": round(aggregate_mlups(cells, args.steps, world, t_e2e), 3), "unit": UNIT,
                "h2d_bytes_per_step": round(8 * cells / args.steps),
-               "d2h_bytes_per_step": round(5 * 8 + 5 * 4 * cells / args.steps),
+               "d2h_bytes_per_step": round(5 * 8 + 5 * 8 * cells / args.steps),
                "seconds": round(t_e2e, 4)}
 
     # ---- reduced-precision storage variants (same workload and step count) ------

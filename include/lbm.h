@@ -158,7 +158,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int n);
 /* Macroscopic fields at the current time, computed on the device from the current
  * populations: phi (Eq. 13), rho (Eq. 14), p (Eq. 30), u (Eq. 29, planar 3N) and mu
  * (Eq. 2).  Only the fields selected in `mask` are written; the others may be NULL.
- * Values are computed in FP32 and widened to double.  Synchronises the stream. */
+ * Values are computed in FP32 and widened to double on the device, then copied into
+ * the caller's buffers (page-locked buffers copy fastest); the widening takes n doubles
+ * of temporary device memory from the context's allocator (LBM_ENOMEM if refused).
+ * Synchronises the stream. */
 lbm_status lbm_read_fields(lbm_ctx* ctx, unsigned mask, double* phi, double* rho,
                            double* p, double* u, double* mu);
 
@@ -167,6 +170,21 @@ lbm_status lbm_read_fields(lbm_ctx* ctx, unsigned mask, double* phi, double* rho
  * reproducible run to run.  Returns LBM_EUNSTABLE (sums still written) if any phi or
  * momentum value is not finite.  Synchronises the stream. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double* sum_phi, double mom[3]);
+
+/* Advance n >= 1 steps and return the sums of lbm_reduce for the resulting state.  In
+ * the coupled model's default variant the last step's stream-collide pass computes them
+ * from the values it stores (streaming with bounce-back only permutes post-collision
+ * populations, a bounced one re-entering its cell with the opposite velocity), so no
+ * extra pass over the state is made; otherwise it runs lbm_step then lbm_reduce.  The
+ * 32 cells of a warp are summed in FP32, everything above in FP64 in a fixed order:
+ * results are reproducible run to run, and agree with lbm_reduce to the FP32 rounding of
+ * those warp sums (about 1e-6 of a warp sum).  Returns LBM_EUNSTABLE (sums still
+ * written) if any contribution is not finite.  Synchronises the stream. */
+lbm_status lbm_step_reduce(lbm_ctx* ctx, int n, double* sum_phi, double mom[3]);
+
+/* lbm_step_reduce without waiting: the 5 doubles of lbm_reduce_async land in out_dev
+ * (same contract) once the stream has passed the n steps. */
+lbm_status lbm_step_reduce_async(lbm_ctx* ctx, int n, double* out_dev);
 
 /* The same sums without waiting: enqueued on the context's stream, they land in
  * out_dev[0..4] = {sum phi, momentum x, y, z, number of cells with a non-finite phi or

@@ -34,6 +34,7 @@ struct lbm_ctx {
                            // gather/scatter, initial u and p
   double* partial = nullptr;  // reduction partials
   double* red = nullptr;      // 5 reduction results
+  double* step_parts = nullptr;  // per-block partials of the fused step sums
 
   // interface-tracking mode (0: coupled): prescribed velocity kind, amplitude, period
   int vel_kind = 0;
@@ -166,8 +167,14 @@ void release(lbm_ctx* c) {
   dev_free(c, c->stage);
   dev_free(c, c->partial);
   dev_free(c, c->red);
+  dev_free(c, c->step_parts);
   c->pop[0] = c->pop[1] = c->phi = c->mu = c->stage = nullptr;
-  c->partial = c->red = nullptr;
+  c->partial = c->red = c->step_parts = nullptr;
+}
+
+// Per-block partials of the fused step sums: 5 doubles per block of kBlock cells.
+size_t step_parts_bytes(long long n) {
+  return static_cast<size_t>(lbm::cell_blocks(n)) * 5 * sizeof(double);
 }
 
 // Pattern of the next step's reads of the current state.
@@ -201,12 +208,12 @@ cudaError_t timed(lbm_ctx* c, int kernel, F&& launch) {
 }
 
 // Copy N floats of a device plane to host doubles.
-lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, std::vector<float>& tmp) {
+// Widen an FP32 device plane to double on the device (into wide, n doubles) and copy
+// it into the caller's host buffer; asynchronous on the context's stream.
+lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, double* wide) {
   const size_t n = static_cast<size_t>(c->geo.n);
-  tmp.resize(n);
-  LBM_CK(c, cudaMemcpyAsync(tmp.data(), dev, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-  LBM_CK(c, cudaStreamSynchronize(c->stream));
-  for (size_t i = 0; i < n; ++i) host[i] = tmp[i];
+  LBM_CK(c, lbm::launch_widen(dev, wide, c->geo.n, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(host, wide, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return LBM_OK;
 }
 
@@ -250,6 +257,49 @@ void lbm::ctx_advance(lbm_ctx* c, int n) {
   c->step += n;
   c->have_prev = true;
 }
+
+namespace {
+
+// One time step; with sums_out the stream-collide pass also reduces the new state into
+// sums_out (5 doubles on the device; coupled default variant only).
+lbm_status step_once(lbm_ctx* c, double* sums_out) {
+  const int pat = read_pattern(c);
+  const float* src = cur_state(c);
+  float* dst = c->params.pattern == LBM_PATTERN_AB ? c->pop[1 - c->cur] : c->pop[c->cur];
+  LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->phi, c->geo, pat, c->stream); }));
+  LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
+  const bool prev = c->have_prev;
+  if (c->vel_kind == LBM_VELOCITY_NONE) {
+    LBM_CK(c, timed(c, 2, [&] {
+             return sums_out ? lbm::launch_collide_sums(src, dst, c->phi, c->mu, c->geo, c->ph,
+                                                         pat, prev, c->step_parts, c->partial,
+                                                         sums_out, c->stream)
+                             : lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat,
+                                                   prev, c->stream);
+           }));
+  } else {
+    const float tf = velocity_time_factor(c, c->step);
+    LBM_CK(c, timed(c, 2, [&] {
+             return lbm::launch_che(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev, tf,
+                                    c->stream);
+           }));
+  }
+  if (c->params.pattern == LBM_PATTERN_AB)
+    c->cur = 1 - c->cur;
+  else
+    c->odd = !c->odd;
+  c->have_prev = true;
+  ++c->step;
+  return LBM_OK;
+}
+
+// Whether the last step of lbm_step_reduce can carry the sums (else a separate pass).
+bool fused_sums(const lbm_ctx* c) {
+  return c->vel_kind == LBM_VELOCITY_NONE &&
+         !(c->params.flags & (LBM_FLAG_SRT_FLOW | LBM_FLAG_D3Q7_STENCIL));
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -301,8 +351,9 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   c->stage = static_cast<float*>(dev_alloc(c, plane * 7));
   c->partial = static_cast<double*>(dev_alloc(c, sizeof(double) * 5 * lbm::kReduceMaxParts));
   c->red = static_cast<double*>(dev_alloc(c, sizeof(double) * 8));
+  c->step_parts = static_cast<double*>(dev_alloc(c, step_parts_bytes(c->geo.n)));
   if (!c->pop[0] || (params->pattern == LBM_PATTERN_AB && !c->pop[1]) || !c->phi || !c->mu ||
-      !c->stage || !c->partial || !c->red) {
+      !c->stage || !c->partial || !c->red || !c->step_parts) {
     release(c);
     delete c;
     return fail(nullptr, LBM_ENOMEM, "device allocation failed");
@@ -352,36 +403,49 @@ lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const do
   return LBM_OK;
 }
 
+
 lbm_status lbm_step(lbm_ctx* c, int n) {
   if (!c) return LBM_EINVAL;
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
   for (int it = 0; it < n; ++it) {
-    const int pat = read_pattern(c);
-    const float* src = cur_state(c);
-    float* dst = c->params.pattern == LBM_PATTERN_AB ? c->pop[1 - c->cur] : c->pop[c->cur];
-    LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->phi, c->geo, pat, c->stream); }));
-    LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
-    const bool prev = c->have_prev;
-    if (c->vel_kind == LBM_VELOCITY_NONE) {
-      LBM_CK(c, timed(c, 2, [&] {
-               return lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev,
-                                          c->stream);
-             }));
-    } else {
-      const float tf = velocity_time_factor(c, c->step);
-      LBM_CK(c, timed(c, 2, [&] {
-               return lbm::launch_che(src, dst, c->phi, c->mu, c->geo, c->ph, pat, prev, tf,
-                                      c->stream);
-             }));
-    }
-    if (c->params.pattern == LBM_PATTERN_AB)
-      c->cur = 1 - c->cur;
-    else
-      c->odd = !c->odd;
-    c->have_prev = true;
-    ++c->step;
+    const lbm_status st = step_once(c, nullptr);
+    if (st != LBM_OK) return st;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_step_reduce_async(lbm_ctx* c, int n, double* out_dev) {
+  if (!c) return LBM_EINVAL;
+  if (n < 1) return fail(c, LBM_EINVAL, "n must be >= 1");
+  if (!out_dev || reinterpret_cast<uintptr_t>(out_dev) % alignof(double) != 0)
+    return fail(c, LBM_EINVAL, "out_dev must be a non-NULL, 8-byte aligned pointer");
+  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (!fused_sums(c)) {
+    const lbm_status st = lbm_step(c, n);
+    return st != LBM_OK ? st : lbm_reduce_async(c, out_dev);
+  }
+  for (int it = 0; it < n; ++it) {
+    const lbm_status st = step_once(c, it == n - 1 ? out_dev : nullptr);
+    if (st != LBM_OK) return st;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_step_reduce(lbm_ctx* c, int n, double* sum_phi, double mom[3]) {
+  if (!c) return LBM_EINVAL;
+  if (!sum_phi || !mom) return fail(c, LBM_EINVAL, "outputs must not be NULL");
+  const lbm_status st = lbm_step_reduce_async(c, n, c->red);
+  if (st != LBM_OK) return st;
+  double h[5];
+  LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  *sum_phi = h[0];
+  mom[0] = h[1];
+  mom[1] = h[2];
+  mom[2] = h[3];
+  if (h[4] > 0) return fail(c, LBM_EUNSTABLE, "non-finite phi or momentum in " +
+                                                  std::to_string(static_cast<long long>(h[4])) + " cells");
   return LBM_OK;
 }
 
@@ -403,16 +467,20 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
     LBM_CK(c, lbm::launch_fields(cur_state(c), phi_now, mu_now, c->stage, c->geo, c->ph,
                                  read_pattern(c), velocity_time_factor(c, c->step), c->stream));
-  std::vector<float> tmp;
+  double* wide = static_cast<double*>(dev_alloc(c, n * sizeof(double)));
+  if (!wide) return fail(c, LBM_ENOMEM, "device allocation failed (read-out staging)");
   lbm_status st = LBM_OK;
-  if (mask & LBM_FIELD_PHI) st = plane_to_host(c, phi_now, phi, tmp);
-  if (st == LBM_OK && (mask & LBM_FIELD_MU)) st = plane_to_host(c, mu_now, mu, tmp);
-  if (st == LBM_OK && (mask & LBM_FIELD_RHO)) st = plane_to_host(c, c->stage, rho, tmp);
-  if (st == LBM_OK && (mask & LBM_FIELD_P)) st = plane_to_host(c, c->stage + s, p, tmp);
+  if (mask & LBM_FIELD_PHI) st = plane_to_host(c, phi_now, phi, wide);
+  if (st == LBM_OK && (mask & LBM_FIELD_MU)) st = plane_to_host(c, mu_now, mu, wide);
+  if (st == LBM_OK && (mask & LBM_FIELD_RHO)) st = plane_to_host(c, c->stage, rho, wide);
+  if (st == LBM_OK && (mask & LBM_FIELD_P)) st = plane_to_host(c, c->stage + s, p, wide);
   for (int a = 0; a < 3 && st == LBM_OK && (mask & LBM_FIELD_U); ++a)
-    st = plane_to_host(c, c->stage + (2 + a) * s, u + a * n, tmp);
-  if (st == LBM_OK) LBM_CK(c, cudaStreamSynchronize(c->stream));
-  return st;
+    st = plane_to_host(c, c->stage + (2 + a) * s, u + a * n, wide);
+  const cudaError_t es = cudaStreamSynchronize(c->stream);
+  dev_free(c, wide);
+  if (st != LBM_OK) return st;
+  if (es != cudaSuccess) return fail_cuda(c, "lbm_read_fields", es);
+  return LBM_OK;
 }
 
 lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
@@ -581,7 +649,7 @@ lbm_status lbm_memory_bytes(const lbm_grid* grid, const lbm_params* params, size
   const size_t plane = static_cast<size_t>((n + 63) / 64 * 64) * sizeof(float);
   const size_t state = lbm::state_bytes(static_cast<int>(n), params->storage);
   *bytes = state * (params->pattern == LBM_PATTERN_AB ? 2 : 1) + plane * 9 +
-           sizeof(double) * (5 * lbm::kReduceMaxParts + 8);
+           sizeof(double) * (5 * lbm::kReduceMaxParts + 8) + step_parts_bytes(n);
   return LBM_OK;
 }
 

@@ -175,11 +175,18 @@ __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ 
 // d_t(phi u), store f+ and g+ (Eqs. 14-34).  src and dst are the same array for the
 // in-place patterns.  All 25 cell-state loads are issued first so that they are in
 // flight together with the stencil loads.
-template <int P, int VAR, int S>
+// With SUMS, sums[0..3] receive the cell's contributions to the global sums of the state
+// after this step (as lbm_reduce defines them): streaming only permutes post-collision
+// values, and a population that meets a wall re-enters its own cell with the opposite
+// velocity, so sum phi = sum of all post-collision f, and the lattice momentum = sum of
+// c_i g_i with c_i negated for the populations that bounce.  Each value is taken as the
+// next step will read it back from storage (16-bit rounding, the slot-0 shift undone).
+template <int P, int VAR, int S, bool SUMS = false>
 __device__ __forceinline__ void collide_cell(const float* src, float* dst,
                                              const float* __restrict__ phi,
                                              const float* __restrict__ mu, const Geometry& geo,
-                                             const Physics& ph, int have_prev, int idx) {
+                                             const Physics& ph, int have_prev, int idx,
+                                             float* sums = nullptr) {
   int x, y, z;
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
@@ -194,6 +201,26 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
   collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
+  if (SUMS) {
+    typedef Elem<S> E;
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#define X(I, O, CX, CY, CZ)                                                  \
+  if (I != 0) {                                                              \
+    const float v = E::get(E::put(g[I]));                                    \
+    const float sv = ((CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo)) ? -v : v;   \
+    if (CX > 0) jx += sv;                                                    \
+    if (CX < 0) jx -= sv;                                                    \
+    if (CY > 0) jy += sv;                                                    \
+    if (CY < 0) jy -= sv;                                                    \
+    if (CZ > 0) jz += sv;                                                    \
+    if (CZ < 0) jz -= sv;                                                    \
+  }
+    LBM_D3Q15_LIST(X)
+#undef X
+    sums[1] = jx;
+    sums[2] = jy;
+    sums[3] = jz;
+  }
   store_g<P, S>(dst, idx, nb, g);
 
   // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
@@ -206,6 +233,14 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   }
 
   collide_d3q7<S != kF32>(ph, f, cs.phi, cs.mu, M.u, dphiu);
+  if (SUMS) {
+    typedef Elem<S> E;
+    float f0 = E::get(E::put(f[0]));
+    if (S != kF32) f0 += cs.phi;  // slot 0 holds f_0 - phi
+    sums[0] = f0 + ((E::get(E::put(f[1])) + E::get(E::put(f[2]))) +
+                    (E::get(E::put(f[3])) + E::get(E::put(f[4]))) +
+                    (E::get(E::put(f[5])) + E::get(E::put(f[6]))));
+  }
   store_f<P, S>(dst, idx, nb, f);
 }
 

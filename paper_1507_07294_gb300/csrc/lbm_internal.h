@@ -37,6 +37,7 @@ cudaError_t launch_gather(const float* src, const float* phi_ref, float* dense, 
 cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
                            int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
+cudaError_t launch_widen(const float* in, double* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
 // Resident blocks per SM of k_collide (kernel 0) or k_phi (kernel 1); 0 on error.
 int resident_blocks_per_sm(int kernel, int storage);
@@ -47,13 +48,14 @@ inline size_t state_bytes(int n, int storage) {
   const int tb = storage == kF32 ? tile_bytes<kF32>() : tile_bytes<kF16>();
   return static_cast<size_t>((n + kTile - 1) / kTile) * tb;
 }
-cudaError_t launch_gather(const float* pop, float* dense, const Geometry& geo, bool odd,
-                          int slot, cudaStream_t st);
-cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
-int reduce_parts(const Geometry& geo);
-// Resident blocks per SM of k_collide (kernel 0) or k_phi (kernel 1); 0 on error.
-int resident_blocks_per_sm(int kernel, int storage);
-cudaError_t launch_reduce(const float* pop, const float* phi, double* partial, double* out,
-                          const Geometry& geo, bool odd, cudaStream_t st);
+// Blocks of a one-cell-per-thread launch over n cells (one partial each in the fused sums).
+int cell_blocks(long long n);
+// Stream-collide of the default model variant that also reduces the state it writes:
+// per-block partials into parts (5 x blocks_for(n) doubles), then the fixed-order
+// reduction through partial (5 x kReduceMaxParts) into out (5 doubles, as launch_reduce).
+cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
+                                const Geometry& geo, const Physics& ph, int pattern,
+                                bool have_prev, double* parts, double* partial, double* out,
+                                cudaStream_t st);
 
 }  // namespace lbm

@@ -66,6 +66,39 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
   collide_cell<P, VAR, S>(src, dst, phi, mu, geo, ph, have_prev, idx);
 }
 
+// Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
+// each block leaves 5 doubles in parts[5 blockIdx.x ..]: sum phi, momentum x, y, z and
+// the count of cells with a non-finite contribution.  The 32 cells of a warp are summed
+// in FP32 by a fixed butterfly (FP64 throughput on this GPU is a small fraction of FP32),
+// the warps of a block and everything above in FP64, in a fixed order.
+template <int P, int S>
+__global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
+    k_collide_sums(const float* src, float* dst, const float* __restrict__ phi,
+                   const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev,
+                   double* __restrict__ parts) {
+  prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
+  const int idx = blockIdx.x * kBlock + threadIdx.x;
+  float s[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (idx < geo.n) {
+    collide_cell<P, 0, S, true>(src, dst, phi, mu, geo, ph, have_prev, idx, s);
+    s[4] = (isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3])) ? 0.0f : 1.0f;
+  }
+  __shared__ double sh[kBlock / 32][5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float v = s[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = static_cast<double>(v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double v = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) v += sh[w][threadIdx.x];
+    parts[blockIdx.x * 5 + threadIdx.x] = v;
+  }
+}
+
 // ------------------------------------------------------------------ k_che ---------
 // Interface tracking with a prescribed velocity (Sec. III A, B): only the D3Q7 lattice
 // evolves (Eq. 4); u is analytic, so the flow lattice and the stencils of phi and mu
@@ -260,6 +293,12 @@ __global__ void __launch_bounds__(kBlock) k_convert(const double* __restrict__ i
   if (idx < n) out[idx] = static_cast<float>(in[idx]);
 }
 
+__global__ void __launch_bounds__(kBlock) k_widen(const float* __restrict__ in,
+                                                  double* __restrict__ out, int n) {
+  const int idx = blockIdx.x * kBlock + threadIdx.x;
+  if (idx < n) out[idx] = static_cast<double>(in[idx]);
+}
+
 // --------------------------------------------------------------- k_reduce ---------
 // Pass 1: block b sums cells b*256 + t, then strides by the grid, in FP64 (fixed
 // order: grid-stride rows, then a fixed shuffle tree).
@@ -321,6 +360,27 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double* __restric
       __syncthreads();
     }
     if (threadIdx.x == 0) out[k] = sh[0];
+    __syncthreads();
+  }
+}
+
+// Block b sums parts [b chunk, (b + 1) chunk) (5 doubles each) in a fixed order.
+__global__ void __launch_bounds__(kBlock) k_reduce_chunks(const double* __restrict__ parts,
+                                                          int nparts, int chunk,
+                                                          double* __restrict__ out) {
+  __shared__ double sh[kBlock];
+  const int b0 = blockIdx.x * chunk;
+  const int b1 = min(nparts, b0 + chunk);
+  for (int k = 0; k < 5; ++k) {
+    double v = 0.0;
+    for (int b = b0 + threadIdx.x; b < b1; b += kBlock) v += parts[b * 5 + k];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x * 5 + k] = sh[0];
     __syncthreads();
   }
 }
@@ -395,6 +455,26 @@ cudaError_t launch_collide(const float* src, float* dst, const float* phi, const
   return cudaGetLastError();
 }
 
+int cell_blocks(long long n) { return static_cast<int>((n + kBlock - 1) / kBlock); }
+
+cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
+                                const Geometry& geo, const Physics& ph, int pattern,
+                                bool have_prev, double* parts, double* partial, double* out,
+                                cudaStream_t st) {
+  const int prev = have_prev ? 1 : 0;
+  LBM_DISPATCH(geo, pattern, k_collide_sums, src, dst, phi, mu, geo, ph, prev, parts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nparts = static_cast<int>(blocks_for(geo.n));
+  const int groups = nparts < kReduceMaxParts ? nparts : kReduceMaxParts;
+  const int chunk = (nparts + groups - 1) / groups;
+  k_reduce_chunks<<<groups, kBlock, 0, st>>>(parts, nparts, chunk, partial);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_final<<<1, kBlock, 0, st>>>(partial, groups, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_che(const float* src, float* dst, const float* phi, const float* mu,
                        const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                        float tf, cudaStream_t st) {
@@ -430,6 +510,11 @@ cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo
 
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st) {
   k_convert<<<blocks_for(n), kBlock, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float* in, double* out, int n, cudaStream_t st) {
+  k_widen<<<blocks_for(n), kBlock, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

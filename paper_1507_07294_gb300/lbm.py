@@ -92,6 +92,8 @@ _SIGNATURES = {
     "lbm_batch_step": (c_int, [c_void_p, POINTER(c_void_p), c_int, c_int]),
     "lbm_batch_set_grid": (c_int, [c_void_p, c_int, c_int]),
     "lbm_reduce_async": (c_int, [c_void_p, c_void_p]),
+    "lbm_step_reduce": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double)]),
+    "lbm_step_reduce_async": (c_int, [c_void_p, c_int, c_void_p]),
     "lbm_batch_get_grid": (c_int, [c_void_p, c_int, POINTER(c_int)]),
     "lbm_batch_set_prefetch": (c_int, [c_void_p, c_int, c_int]),
     "lbm_batch_set_split": (c_int, [c_void_p, c_longlong]),
@@ -237,14 +239,25 @@ def lbm_step(ctx: Context, n: int = 1) -> None:
     _check(lib, lib.lbm_step(ctx.handle, int(n)), ctx.handle)
 
 
-def lbm_read_fields(ctx: Context, mask: int = LBM_FIELD_ALL) -> dict:
-    """Returns a dict of float64 arrays shaped [z, y, x] (u: [3, z, y, x])."""
+def lbm_read_fields(ctx: Context, mask: int = LBM_FIELD_ALL, out: Optional[dict] = None) -> dict:
+    """Returns a dict of float64 arrays shaped [z, y, x] (u: [3, z, y, x]).  `out` may
+    hold preallocated float64 arrays (e.g. page-locked) for the selected fields."""
     lib = load_library()
+    given = out or {}
     out = {}
     bufs = {}
     for name, bit, comps in (("phi", LBM_FIELD_PHI, 1), ("rho", LBM_FIELD_RHO, 1),
                              ("p", LBM_FIELD_P, 1), ("u", LBM_FIELD_U, 3), ("mu", LBM_FIELD_MU, 1)):
-        bufs[name] = np.empty(comps * ctx.n) if mask & bit else None
+        if not mask & bit:
+            bufs[name] = None
+        elif name in given:
+            a = given[name]
+            if a.dtype != np.float64 or a.size != comps * ctx.n or not a.flags.c_contiguous:
+                raise ValueError(f"out[{name!r}] must be a contiguous float64 array of "
+                                 f"{comps * ctx.n} values")
+            bufs[name] = a.reshape(-1)
+        else:
+            bufs[name] = np.empty(comps * ctx.n)
     _check(lib, lib.lbm_read_fields(ctx.handle, mask, _ptr(bufs["phi"]), _ptr(bufs["rho"]),
                                     _ptr(bufs["p"]), _ptr(bufs["u"]), _ptr(bufs["mu"])), ctx.handle)
     for name, a in bufs.items():
@@ -266,6 +279,28 @@ def lbm_reduce(ctx: Context, check: bool = True):
     if st not in (LBM_OK, LBM_EUNSTABLE):
         _check(lib, st, ctx.handle)
     return s.value, np.array(mom[:]), st
+
+
+def lbm_step_reduce(ctx: Context, n: int = 1, check: bool = True):
+    """Advances n steps; returns (sum_phi, momentum[3]) of the new state (the last
+    step's stream-collide pass computes them).  check=False: like lbm_reduce."""
+    lib = load_library()
+    s = c_double()
+    mom = (c_double * 3)()
+    st = lib.lbm_step_reduce(ctx.handle, int(n), ctypes.byref(s), mom)
+    if check:
+        _check(lib, st, ctx.handle)
+        return s.value, np.array(mom[:])
+    if st not in (LBM_OK, LBM_EUNSTABLE):
+        _check(lib, st, ctx.handle)
+    return s.value, np.array(mom[:]), st
+
+
+def lbm_step_reduce_async(ctx: Context, n: int, out_dev: int) -> None:
+    """Advances n steps and enqueues the sums of the new state into 5 doubles at device
+    address out_dev.  No synchronisation."""
+    lib = load_library()
+    _check(lib, lib.lbm_step_reduce_async(ctx.handle, int(n), c_void_p(out_dev)), ctx.handle)
 
 
 def lbm_reduce_async(ctx: Context, out_dev: int) -> None:

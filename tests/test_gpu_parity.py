@@ -304,3 +304,20 @@ def test_autotune_changes_speed_not_results(L):
         sb = b.state()
     for x, y in zip(sa[:3], sb[:3]):
         assert np.array_equal(x, y)
+
+
+def test_read_fields_into_given_buffers(L):
+    """Preallocated (here page-locked) output arrays receive the same values."""
+    import torch
+    w = I.perturbed(I.droplet(n=12, R=4.0, nx=13), seed=23, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w) as s:
+        s.step(3)
+        ref = s.fields()
+        bufs = {"phi": torch.empty(w.cells, dtype=torch.float64, pin_memory=True).numpy(),
+                "u": np.empty((3,) + w.shape)}
+        got = L.lbm_read_fields(s.ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_MU, out=bufs)
+        with pytest.raises(ValueError):
+            L.lbm_read_fields(s.ctx, L.LBM_FIELD_PHI, out={"phi": np.empty(3)})
+    assert np.shares_memory(got["phi"], bufs["phi"]) and np.shares_memory(got["u"], bufs["u"])
+    for k in ("phi", "u", "mu"):
+        assert np.array_equal(got[k], ref[k])
