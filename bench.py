@@ -60,9 +60,11 @@ STEP_BYTES_PER_CELL_16 = COLLIDE_BYTES_PER_CELL_16 + (7 * 2 + 4 + 4) + 8
 # the kernel source it was taken on (hash of csrc/lbm_device.cuh, lbm_cells.cuh and
 # lbm_kernels.cu).
 NCU_TRAFFIC = {
-    # profiles/step_kernels_rt128x128x512_full.md: 1705.0 MB per launch over 8,388,608
+    # profiles/step_kernels_rt128x128x512_full.md: 1705.3 MB per launch over 8,388,608
     # cells (ncu --set full on the 128x128x512 case, scaled by cells to the benchmark)
-    "k_collide": {"bytes_per_cell": 203.25, "kernel_sha": "1184771e0eac09d0"},
+    "k_collide": {"bytes_per_cell": 203.29, "kernel_sha": "a48b5ac6d371bc46"},
+    # profiles/collide_fp16_rt128x128x512_full.md: 971.0 MB per launch, FP16 storage
+    "k_collide_fp16": {"bytes_per_cell": 115.76, "kernel_sha": "a48b5ac6d371bc46"},
 }
 
 WORKLOADS = {
@@ -241,7 +243,7 @@ def config_dict(args, w, world):
     spec = WORKLOADS[args.workload]
     return {"workload": f"{args.workload}: {spec['desc']}",
             "grid": [w.nx, w.ny, w.nz], "cells": w.cells, "walls_z": bool(w.walls_z),
-            "storage": "fp32", "pattern": getattr(args, "pattern", "ab"),
+            "storage": getattr(args, "storage", "fp32"), "pattern": getattr(args, "pattern", "ab"),
             "l2": f"state {w.cells * 100 / 1e9:.1f} GB (f, g, phi u) > 129 MB L2: no flush needed",
             "parallelism": f"replicas x{world} (independent runs per GPU)"}
 
@@ -347,7 +349,9 @@ def run_ours(args):
     spec = WORKLOADS[args.workload]
     w = I.rayleigh_taylor(W=spec["W"], Re=spec["Re"])
     stream = torch.cuda.current_stream()
-    solver = L.Solver(w, stream=stream.cuda_stream, pattern=args.pattern)
+    if args.storage != "fp32" and args.pattern != "ab":
+        raise SystemExit("16-bit storage runs pattern ab only")
+    solver = L.Solver(w, stream=stream.cuda_stream, pattern=args.pattern, storage=args.storage)
     ctx = solver.ctx
 
     group = RankGroup(world, rank, "nccl")
@@ -393,9 +397,12 @@ def run_ours(args):
     value = aggregate_mlups(cells, args.steps, world, elapsed_ms * 1e-3)
     coll_ms = kernels["k_collide"]["mean_ms"]
     peak, peak_kind = measured_peaks()
-    achieved = COLLIDE_BYTES_PER_CELL * cells / (coll_ms * 1e-3) / 1e9
+    wide = args.storage == "fp32"
+    coll_bytes = COLLIDE_BYTES_PER_CELL if wide else COLLIDE_BYTES_PER_CELL_16
+    step_bytes = STEP_BYTES_PER_CELL if wide else STEP_BYTES_PER_CELL_16
+    achieved = coll_bytes * cells / (coll_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
-    tr = NCU_TRAFFIC.get("k_collide")
+    tr = NCU_TRAFFIC.get("k_collide" if wide else f"k_collide_{args.storage}")
     traffic = round(tr["bytes_per_cell"] * cells) if tr and tr.get("kernel_sha") == src_hash else None
 
     # ---- end-to-end region through the C ABI with host buffers ---------------
@@ -422,7 +429,7 @@ def run_ours(args):
 
     # ---- reduced-precision storage variants (same workload and step count) ------
     variants = None
-    if not args.no_variants:
+    if not args.no_variants and args.storage == "fp32":
         solver.close()
         variants = {}
         for storage in ("fp16", "bf16"):
@@ -474,10 +481,10 @@ def run_ours(args):
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                              "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                              "kernel": "k_collide",
-                             "bytes_per_cell": COLLIDE_BYTES_PER_CELL,
+                             "bytes_per_cell": coll_bytes,
                              "peak_source": f"{peak_kind} HBM copy bandwidth"},
-                "step_bytes_per_cell": STEP_BYTES_PER_CELL,
-                "step_hbm_frac": round(STEP_BYTES_PER_CELL * cells * args.steps /
+                "step_bytes_per_cell": step_bytes,
+                "step_hbm_frac": round(step_bytes * cells * args.steps /
                                        (elapsed_ms * 1e-3) / 1e9 / peak, 4),
                 "kernels": kernels,
                 "tuning": {k: v["value"] for k, v in tuning.items()} if tuning else None,
@@ -501,6 +508,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rt256")
     ap.add_argument("--pattern", choices=("ab", "aa"), default="ab",
                     help="population storage: two arrays (ab) or in place (aa)")
+    ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
+                    help="population storage of the main run (arithmetic is FP32 in all)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
