@@ -172,9 +172,9 @@ void release(lbm_ctx* c) {
   c->partial = c->red = c->step_parts = nullptr;
 }
 
-// Per-block partials of the fused step sums: 5 doubles per block of kBlock cells.
+// Per-warp partials of the fused step sums: 5 doubles per 32 cells.
 size_t step_parts_bytes(long long n) {
-  return static_cast<size_t>(lbm::cell_blocks(n)) * 5 * sizeof(double);
+  return static_cast<size_t>(lbm::cell_warps(n)) * 5 * sizeof(double);
 }
 
 // Pattern of the next step's reads of the current state.

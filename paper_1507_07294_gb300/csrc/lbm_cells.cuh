@@ -203,20 +203,25 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
   if (SUMS) {
     typedef Elem<S> E;
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#define X(I, O, CX, CY, CZ)                                                  \
-  if (I != 0) {                                                              \
-    const float v = E::get(E::put(g[I]));                                    \
-    const float sv = ((CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo)) ? -v : v;   \
-    if (CX > 0) jx += sv;                                                    \
-    if (CX < 0) jx -= sv;                                                    \
-    if (CY > 0) jy += sv;                                                    \
-    if (CY < 0) jy -= sv;                                                    \
-    if (CZ > 0) jz += sv;                                                    \
-    if (CZ < 0) jz -= sv;                                                    \
+    float v[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) v[i] = E::get(E::put(g[i]));
+    // sum c_i v_i (corners (1,1,1), (1,1,-1), (1,-1,1), (1,-1,-1) and their opposites)
+    const float a7 = v[7] - v[8], a9 = v[9] - v[10], a11 = v[11] - v[12], a13 = v[13] - v[14];
+    float jx = (v[1] - v[2]) + ((a7 + a9) + (a11 + a13));
+    float jy = (v[3] - v[4]) + ((a7 + a9) - (a11 + a13));
+    float jz = (v[5] - v[6]) + ((a7 - a9) + (a11 - a13));
+    if (nb.wlo || nb.whi) {
+      // populations leaving through a wall come back reversed: take 2 c_i v_i off
+#define X(I, O, CX, CY, CZ)                                    \
+  if ((CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo)) {              \
+    jx -= 2.0f * CX * v[I];                                    \
+    jy -= 2.0f * CY * v[I];                                    \
+    jz -= 2.0f * CZ * v[I];                                    \
   }
-    LBM_D3Q15_LIST(X)
+      LBM_D3Q15_LIST(X)
 #undef X
+    }
     sums[1] = jx;
     sums[2] = jy;
     sums[3] = jz;

@@ -48,10 +48,10 @@ inline size_t state_bytes(int n, int storage) {
   const int tb = storage == kF32 ? tile_bytes<kF32>() : tile_bytes<kF16>();
   return static_cast<size_t>((n + kTile - 1) / kTile) * tb;
 }
-// Blocks of a one-cell-per-thread launch over n cells (one partial each in the fused sums).
-int cell_blocks(long long n);
+// Warps of a one-cell-per-thread launch over n cells (one partial each in the fused sums).
+int cell_warps(long long n);
 // Stream-collide of the default model variant that also reduces the state it writes:
-// per-block partials into parts (5 x blocks_for(n) doubles), then the fixed-order
+// per-warp partials into parts (5 x cell_warps(n) doubles), then the fixed-order
 // reduction through partial (5 x kReduceMaxParts) into out (5 doubles, as launch_reduce).
 cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
                                 const Geometry& geo, const Physics& ph, int pattern,

@@ -67,10 +67,11 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
 }
 
 // Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
-// each block leaves 5 doubles in parts[5 blockIdx.x ..]: sum phi, momentum x, y, z and
-// the count of cells with a non-finite contribution.  The 32 cells of a warp are summed
-// in FP32 by a fixed butterfly (FP64 throughput on this GPU is a small fraction of FP32),
-// the warps of a block and everything above in FP64, in a fixed order.
+// each warp leaves 5 doubles in parts[5 w ..] (w = its first cell / 32): sum phi,
+// momentum x, y, z and the count of cells with a non-finite contribution.  The 32 cells
+// of a warp are summed in FP32 by a fixed butterfly (FP64 throughput on this GPU is a
+// small fraction of FP32, and no block barrier holds finished warps back); everything
+// above in FP64, in a fixed order.
 template <int P, int S>
 __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
     k_collide_sums(const float* src, float* dst, const float* __restrict__ phi,
@@ -78,24 +79,23 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
                    double* __restrict__ parts) {
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
-  float s[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if ((idx & ~31) >= geo.n) return;  // the whole warp lies beyond the grid
+  float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  bool bad = false;
   if (idx < geo.n) {
     collide_cell<P, 0, S, true>(src, dst, phi, mu, geo, ph, have_prev, idx, s);
-    s[4] = (isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3])) ? 0.0f : 1.0f;
+    bad = !(isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3]));
   }
-  __shared__ double sh[kBlock / 32][5];
+  const unsigned nbad = __popc(__ballot_sync(0xffffffffu, bad));
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    float v = s[k];
+  for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = static_cast<double>(v);
-  }
-  __syncthreads();
-  if (threadIdx.x < 5) {
-    double v = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) v += sh[w][threadIdx.x];
-    parts[blockIdx.x * 5 + threadIdx.x] = v;
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+  if ((threadIdx.x & 31) == 0) {
+    double* out = parts + static_cast<size_t>(idx >> 5) * 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = static_cast<double>(s[k]);
+    out[4] = static_cast<double>(nbad);
   }
 }
 
@@ -455,7 +455,7 @@ cudaError_t launch_collide(const float* src, float* dst, const float* phi, const
   return cudaGetLastError();
 }
 
-int cell_blocks(long long n) { return static_cast<int>((n + kBlock - 1) / kBlock); }
+int cell_warps(long long n) { return static_cast<int>((n + 31) / 32); }
 
 cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
                                 const Geometry& geo, const Physics& ph, int pattern,
@@ -465,7 +465,7 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
   LBM_DISPATCH(geo, pattern, k_collide_sums, src, dst, phi, mu, geo, ph, prev, parts);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nparts = static_cast<int>(blocks_for(geo.n));
+  const int nparts = cell_warps(geo.n);
   const int groups = nparts < kReduceMaxParts ? nparts : kReduceMaxParts;
   const int chunk = (nparts + groups - 1) / groups;
   k_reduce_chunks<<<groups, kBlock, 0, st>>>(parts, nparts, chunk, partial);

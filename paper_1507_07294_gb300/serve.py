@@ -301,7 +301,8 @@ class GpuEngine:
     def open(self, req: Request):
         w = workload_of(req, phi0=self.phi0(req.grid))
         st = self._free_streams.pop() if self._free_streams else self.torch.cuda.Stream()
-        s = self.lbm.Solver(w, stream=st.cuda_stream, storage=self.storage)
+        with self.torch.cuda.nvtx.range(f"admit {req.rid}"):
+            s = self.lbm.Solver(w, stream=st.cuda_stream, storage=self.storage)
         self._stream_of[id(s)] = st
         return s
 
@@ -312,7 +313,8 @@ class GpuEngine:
         solver.step(n)
 
     def step_batch(self, solvers, n: int) -> None:
-        self.batch.step(solvers, n)
+        with self.torch.cuda.nvtx.range(f"quantum {len(solvers)} runs"):
+            self.batch.step(solvers, n)
 
     def check(self, solver) -> None:
         """Enqueues the run's FP64 sums (lbm_reduce_async) and their copy to the host."""
@@ -352,14 +354,15 @@ class GpuEngine:
     def finish(self, solver):
         """Reads the run's result; a non-finite state marks it unstable."""
         lbm = self.lbm
-        try:
-            totals = solver.reduce()
-            stable = True
-        except lbm.LbmError as e:
-            if e.status != lbm.LBM_EUNSTABLE:
-                raise
-            totals, stable = None, False
-        phi = solver.fields(lbm.LBM_FIELD_PHI)["phi"] if self.keep_phi else None
+        with self.torch.cuda.nvtx.range("read-out"):
+            try:
+                totals = solver.reduce()
+                stable = True
+            except lbm.LbmError as e:
+                if e.status != lbm.LBM_EUNSTABLE:
+                    raise
+                totals, stable = None, False
+            phi = solver.fields(lbm.LBM_FIELD_PHI)["phi"] if self.keep_phi else None
         solver.close()
         self._checks.pop(id(solver), None)
         self._free_streams.append(self._stream_of.pop(id(solver)))
