@@ -248,7 +248,8 @@ lbm_status lbm_field_sum_noalloc(const float* field, long long n, double* out,
                                  void* cuda_stream);
 
 /* Device bytes lbm_create would allocate for `grid` and `params` (same checks as
- * lbm_create); lets a scheduler admit runs against a memory budget. */
+ * lbm_create); lets a scheduler admit runs against a memory budget.  Transient
+ * staging (lbm_init_phi: n doubles; lbm_read_fields: n doubles) is not included. */
 lbm_status lbm_memory_bytes(const lbm_grid* grid, const lbm_params* params, size_t* bytes);
 
 /* Release all device memory of the context and the context itself. */
@@ -257,11 +258,12 @@ lbm_status lbm_destroy(lbm_ctx* ctx);
 /* ---------------------------------------------------------------------------------
  * Batches: many runs advanced together.  The paper has no counterpart; this serves
  * many simulations on one GPU.  lbm_batch_step(b, runs, n, steps) advances every run
- * by `steps` time steps with one launch per pass per time step for all of them: a
- * persistent grid strides over (run, block) work items read from a device table, and
- * the launches of a batch step are a CUDA graph instantiated once per (steps, grid
- * sizes, storage type) and replayed for any run set.  Results are those of lbm_step on
- * each run alone (same per-cell code).  Runs need LBM_PATTERN_AB, the coupled model
+ * by `steps` time steps with one launch per pass per time step for all of them: each
+ * launch takes (run, block) work items listed in a device table, and the launches of
+ * a batch step are a CUDA graph instantiated once per launch shape (steps, storage
+ * type, grid sizes, prefetch distances) and replayed for any run set with that shape.
+ * Each run's state comes out bit for bit as lbm_step alone would leave it (same
+ * per-cell device code), whatever shares the launch.  Runs need LBM_PATTERN_AB, the coupled model
  * (no prescribed velocity), no LBM_FLAG_SRT_FLOW / LBM_FLAG_D3Q7_STENCIL, one storage
  * type per batch, at most 256 per call, and at least one step taken since lbm_init_phi
  * (the first step, with d_t(phi u) = 0, goes through lbm_step); LBM_EINVAL otherwise.
