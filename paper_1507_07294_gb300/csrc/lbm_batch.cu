@@ -4,13 +4,16 @@
 // A batch step of n time steps launches, n times, the three passes (order parameter,
 // chemical potential, fused stream-collide) each ONCE for every run of the batch.  The
 // runs' descriptors (geometry, physics, array pointers, parity) sit in a device table;
-// each pass has a persistent grid whose thread blocks stride over a work list of
-// (run, block-of-that-run) items, so runs of uneven size share the launch and small runs
-// no longer pay a launch each.  Because the kernels read the run set from the table, the
-// 3n launches of a batch step are captured once into a CUDA graph per (n, grid sizes,
-// storage type) and replayed for any run set: between replays the host only rewrites the
-// table.  The per-cell arithmetic is the same device code as the single-run kernels
-// (lbm_cells.cuh).
+// each pass's blocks take (run, block-of-that-run) work items from it -- a persistent
+// grid striding over the items, or one block per item -- so runs of uneven size share
+// the launch and small runs no longer pay a launch each.  Because the kernels read the
+// run set from the table, the 3n launches of a batch step are captured once into a CUDA
+// graph per launch shape and replayed for any run set with that shape: between replays
+// the host only rewrites the table.  Runs of at least a set size (they fill the GPU
+// alone, and the single-run kernels read their parameters from the constant bank rather
+// than shared memory) can instead take their own launches on their own streams, which
+// then overlap the shared ones.  The per-cell arithmetic is the same device code as the
+// single-run kernels (lbm_cells.cuh), so results are bit-identical to lbm_step's.
 #include <cuda_runtime.h>
 
 #include <algorithm>

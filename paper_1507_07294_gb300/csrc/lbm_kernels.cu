@@ -7,8 +7,12 @@
 //   k_mu       mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2, Eq. 36)
 //   k_collide  fused: pull f and g, stencils of phi and mu, forces, u and p, both MRT
 //              collisions, d_t(phi u), store f+ and g+ (Eqs. 14-34)
-// plus initialisation, field read-out, state gather/scatter and the FP64 reduction.
-// Every kernel is templated on the population storage pattern (lbm_device.cuh).
+// plus k_collide_sums (k_collide that also sums the state it writes, for
+// lbm_step_reduce), k_che (interface tracking with a prescribed velocity),
+// initialisation, field read-out, state gather/scatter and the FP64 reduction.
+// Every kernel is templated on the population storage pattern and type
+// (lbm_device.cuh); the per-cell bodies live in lbm_cells.cuh, shared with the batched
+// kernels.
 #include <cuda_runtime.h>
 
 #include "lbm_cells.cuh"

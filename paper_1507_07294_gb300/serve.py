@@ -8,9 +8,11 @@ lbm_memory_bytes), and advances all admitted runs together in quanta of Q time s
 with one batched launch per pass (lbm_batch_step).  A run's first few steps are taken
 alone (lbm_step) -- the first step after initialisation has its own time-derivative
 rule (d_t(phi u) = 0) and the rest of that chunk aligns the run's remaining steps to a
-multiple of Q, so that every admitted run takes part in every quantum.  After each
-quantum, runs that are done are read out (the order-parameter field plus the FP64 mass
-and momentum sums) and their memory is returned to the budget.
+multiple of Q, so that every admitted run takes part in every quantum.  Runs that are
+done are read out (the order-parameter field plus the FP64 mass and momentum sums) and
+their memory is returned to the budget.  The loop is pipelined (the next quantum is
+queued before the host reads out the last one's finished runs), and every few quanta
+each run's FP64 sums are checked so that a diverged run stops early.
 
 The one-at-a-time baseline takes the same requests in arrival order and runs each to
 completion alone with lbm_step, one run on the device at a time (same quanta, same
@@ -21,7 +23,6 @@ sync / finish / footprint), so it runs unchanged against a fake engine on the CP
 """
 from __future__ import annotations
 
-import math
 import time
 from collections import deque
 from dataclasses import dataclass, field
