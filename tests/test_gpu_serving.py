@@ -249,3 +249,24 @@ def test_server_stops_a_diverging_run(L):
         s.step(300)
         assert np.array_equal(s.fields(L.LBM_FIELD_PHI)["phi"], out[1].result["phi"])
     eng.close()
+
+
+def test_batch_limits(L):
+    """At most 256 runs per call; negative sizes and empty calls are refused."""
+    w = I.droplet(n=4, R=1.5)
+    runs = [L.Solver(w) for _ in range(257)]
+    for s in runs:
+        s.step(1)
+    with L.Batch() as b:
+        with pytest.raises(L.LbmError, match="256"):
+            b.step(runs, 1)
+        b.step(runs[:256], 1)
+        with pytest.raises(L.LbmError):
+            b.step([], 1)
+        with pytest.raises(L.LbmError):
+            b.set_split(-1)
+        with pytest.raises(L.LbmError):
+            b.step(runs[:2], -1)
+    assert runs[0].t == 2 and runs[256].t == 1
+    for s in runs:
+        s.close()
