@@ -268,9 +268,13 @@ def run_serving(args, rank: int) -> dict:
                          args.serve_load)
     budget = int(args.serve_budget_gb * 1e9)
     res = {}
+    # runs that take their own launches (the tuned size split) count as large
+    large_cells = tuned.get("split_cells") or max(g[0] * g[1] * g[2] for g in S.GRIDS)
+    max_large = args.serve_max_large or None
     for name, batched in (("batched", True), ("one_at_a_time", False)):
         srv = S.Server(eng, budget, max_runs=args.serve_slots, quantum=args.serve_quantum,
-                       batched=batched)
+                       batched=batched, max_large=max_large if batched else None,
+                       large_cells=large_cells)
         outs = srv.serve(loaded)
         summ = S.summarize(outs)
         by_rid = {r.rid: r for r in loaded}
@@ -289,6 +293,7 @@ def run_serving(args, rank: int) -> dict:
         "sigma": [1e-3, 1e-2], "offered_load_x_one_at_a_time": args.serve_load,
         "arrival_span_s": round(loaded[-1].arrival, 3), "budget_gb": args.serve_budget_gb,
         "max_runs": args.serve_slots, "quantum_steps": args.serve_quantum,
+        "max_large_runs": max_large, "large_cells": large_cells,
         "alone_ms_per_step": {"x".join(map(str, g)): round(v[0] * 1e3, 4)
                               for g, v in model.items()},
         "batch_tuning": {k: v for k, v in tuned.items() if not k.endswith("_ms")},
@@ -526,6 +531,9 @@ def main(argv=None):
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-quantum", type=int, default=64)
+    ap.add_argument("--serve-max-large", type=int, default=2,
+                    help="at most this many large runs (those that take their own "
+                         "launches) at once in the batched server (0: no cap)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

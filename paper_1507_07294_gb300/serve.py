@@ -142,13 +142,24 @@ class Server:
 
     def __init__(self, engine, budget_bytes: int, max_runs: int = 16, quantum: int = 64,
                  batched: bool = True, check_every: int = 2,
+                 max_large: Optional[int] = None, large_cells: int = 0,
                  clock: Callable[[], float] = time.perf_counter,
                  sleep: Callable[[float], None] = time.sleep):
         """check_every: every that many quanta each stepping run's FP64 sums are
         enqueued (lbm_reduce_async); a run found non-finite is stopped and reported
-        unstable without taking its remaining steps (0: never check)."""
+        unstable without taking its remaining steps (0: never check).
+
+        max_large: at most this many runs of at least `large_cells` cells on the device
+        at once (None: no cap).  Large runs fill the GPU by themselves, so sharing it
+        among many of them only stretches each; a large request held back by the cap
+        lets later small requests pass it, and is admitted as soon as a large run
+        leaves."""
         if quantum < 1 or max_runs < 1:
             raise ValueError("quantum and max_runs must be >= 1")
+        if max_large is not None and max_large < 1:
+            raise ValueError("max_large must be >= 1 or None")
+        self.max_large = max_large
+        self.large_cells = int(large_cells)
         self.check_every = check_every
         self.stopped = 0
         self.engine = engine
@@ -161,6 +172,9 @@ class Server:
         self.peak_bytes = 0
         self.peak_runs = 0
         self.quanta = 0
+
+    def _is_large(self, r: Request) -> bool:
+        return self.max_large is not None and r.cells >= self.large_cells
 
     def serve(self, requests: Sequence[Request]) -> List[Outcome]:
         """Serve the requests (arrival times relative to the call) and return their
@@ -185,13 +199,22 @@ class Server:
             t = now()
             while pending and pending[0].arrival <= t:
                 waiting.append(pending.popleft())
-            # admission: first come first served while a slot and the budget allow
-            held = len(active) + (len(inflight[1]) if inflight else 0)
+            # admission: first come first served while a slot and the budget allow; a
+            # large request over the large-run cap is passed over, not waited for
+            held_runs = active + (inflight[1] if inflight else [])
+            held = len(held_runs)
+            large = sum(self._is_large(a[0]) for a in held_runs)
+            passed = deque()
             while waiting and held < self.max_runs:
+                if (self.max_large is not None and self._is_large(waiting[0])
+                        and large >= self.max_large):
+                    passed.append(waiting.popleft())
+                    continue
                 need = self.engine.footprint(waiting[0])
                 if used + need > self.budget:
                     break
                 r = waiting.popleft()
+                large += self._is_large(r)
                 admitted = now()
                 h = self.engine.open(r)
                 used += need
@@ -200,6 +223,8 @@ class Server:
                 if first:
                     self.engine.step_alone(h, first)
                 active.append([r, h, r.steps - first, need, admitted])
+            passed.extend(waiting)
+            waiting = passed  # the passed-over large requests keep their place in line
             self.peak_bytes = max(self.peak_bytes, used)
             self.peak_runs = max(self.peak_runs, held)
             # launch this quantum (and, every check_every quanta, the divergence checks)

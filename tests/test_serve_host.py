@@ -229,3 +229,34 @@ def test_footprint_grows_with_the_grid():
     # populations (22 + 3 slots x 2 arrays) and phi, mu: about 216 B per cell and more
     assert all(200 < b < 300 for b in per_cell)
     assert per_cell[-1] == pytest.approx(per_cell[-2], rel=0.02)
+
+
+def test_large_run_cap():
+    """With max_large = 1 at most one large run is open at a time; small requests pass
+    a held-back large one; large requests keep their order among themselves."""
+    reqs = _reqs(n=60, gap=0.0005, steps=(20, 200))
+    big = 16 * 16 * 64
+
+    class Counting(FakeEngine):
+        def __init__(self):
+            super().__init__()
+            self.max_large_open = 0
+
+        def open(self, r):
+            h = super().open(r)
+            self.max_large_open = max(self.max_large_open,
+                                      sum(c >= big for (_, _, c) in self.open_runs))
+            return h
+
+    eng = Counting()
+    srv = _server(eng, budget_bytes=10**9, max_runs=8, quantum=8, max_large=1,
+                  large_cells=big)
+    out = srv.serve(reqs)
+    assert len(out) == 60 and eng.max_large_open == 1
+    larges = sorted((o for o in out if o.cells >= big), key=lambda o: o.arrival)
+    assert all(a.admitted <= b.admitted for a, b in zip(larges, larges[1:]))
+    passed = [o for o in out if o.cells < big and any(
+        l.arrival < o.arrival and l.admitted > o.admitted for l in larges)]
+    assert passed, "small requests should overtake a large one held by the cap"
+    with pytest.raises(ValueError):
+        _server(FakeEngine(), budget_bytes=10**9, max_large=0)
