@@ -92,3 +92,35 @@ def test_reduced_precision_tracking_mode(L, storage):
     d = float(np.abs(gf["phi"] - o.fields()["phi"]).max())
     print(f"deformation {storage}: max|dphi| {d:.3e}")
     assert d <= TOL[storage][0]
+
+
+# Bubble-front and spike-tip positions, in units of W, against the FP64 oracle's
+# (tests/golden/rt64_fronts.txt; Rayleigh-Taylor on 64 x 64 x 256, At = 0.5,
+# sigma = 1e-4, t* = 0.5 and 1).  Measured on GB300 at Re = 4000, t* = 1: FP32 1e-6,
+# FP16 5e-5, BF16 7e-4 (bubble) from the oracle's positions.
+FRONT_TOL = {"fp32": 2e-4, "fp16": 1e-3, "bf16": 5e-3}
+
+
+def _golden_fronts():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "rt64_fronts.txt")
+    rows = np.loadtxt(path, ndmin=2)
+    cases = {}
+    for re, step, _, bubble, spike in rows:
+        cases.setdefault(float(re), []).append((int(step), bubble, spike))
+    return cases
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_rayleigh_taylor_front_positions(L, storage):
+    from paper_1507_07294_gb300 import diagnostics as Dg
+    for re, rows in sorted(_golden_fronts().items()):
+        w = I.rayleigh_taylor(W=64, Re=re)
+        with L.Solver(w, storage=storage) as s:
+            for step, bubble, spike in rows:
+                s.step(step - s.t)
+                b, sp = Dg.rt_fronts(s.fields(L.LBM_FIELD_PHI)["phi"], 64)
+                print(f"Re {re:g} step {step} {storage}: bubble {b:.6f} (oracle {bubble:.6f}),"
+                      f" spike {sp:.6f} (oracle {spike:.6f})")
+                assert abs(b - bubble) <= FRONT_TOL[storage]
+                assert abs(sp - spike) <= FRONT_TOL[storage]
