@@ -41,7 +41,8 @@ typedef enum {
   LBM_ENOMEM = 2,     /* the allocator returned NULL                               */
   LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error)    */
   LBM_EUNSTABLE = 4,  /* a non-finite value was found by lbm_reduce                */
-  LBM_ETIMEOUT = 5,   /* reserved: a device-side wait ran out                      */
+  LBM_ETIMEOUT = 5,   /* a bounded device-side wait ran out (reported by the next  */
+                      /* lbm_reduce, lbm_step_reduce or lbm_read_fields)          */
   LBM_EBUSY = 6       /* reserved                                                  */
 } lbm_status;
 
@@ -213,10 +214,15 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * LBM_TUNE_PREFETCH_COLLIDE / LBM_TUNE_PREFETCH_PHI: how many thread blocks ahead the
  * fused stream-collide kernel / the order-parameter kernel prefetch cell data into L2
  * (0 disables).  Default: one wave, the number of SMs times the kernel's resident
- * blocks per SM, set by lbm_create.  lbm_set_tuning returns LBM_EINVAL for an unknown
- * parameter or a negative value. */
+ * blocks per SM, set by lbm_create.
+ * LBM_TUNE_MU_TMA: 1 (default) lets the chemical-potential pass fetch its halo bricks
+ * with TMA tensor copies, 0 uses plain loads; the TMA path exists when nx is a multiple
+ * of 32 (and >= 40), ny a multiple of 8 (and >= 10) and nz >= 18, and lbm_get_tuning
+ * reports 1 only while it is in use.  Both give identical results.
+ * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */
 #define LBM_TUNE_PREFETCH_COLLIDE 0
 #define LBM_TUNE_PREFETCH_PHI 1
+#define LBM_TUNE_MU_TMA 2
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 

@@ -1,6 +1,8 @@
 // C ABI of the solver (declared in include/lbm.h): context life cycle, parameter
 // mapping, allocation through the caller's allocator, and the launch sequence of one
 // time step.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -8,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -33,8 +36,13 @@ struct lbm_ctx {
   float* stage = nullptr;  // 7 planes: field read-out (rho, p, u, phi, mu), state
                            // gather/scatter, initial u and p
   double* partial = nullptr;  // reduction partials
-  double* red = nullptr;      // 5 reduction results
-  double* step_parts = nullptr;  // per-block partials of the fused step sums
+  double* red = nullptr;      // 5 reduction results; red[7] holds the device error word
+  double* step_parts = nullptr;  // per-warp partials of the fused step sums
+
+  // TMA descriptor of phi for the chemical-potential pass (when the grid allows it)
+  CUtensorMap phi_map{};
+  bool have_phi_map = false;
+  bool use_phi_map = true;
 
   // interface-tracking mode (0: coupled): prescribed velocity kind, amplitude, period
   int vel_kind = 0;
@@ -172,6 +180,51 @@ void release(lbm_ctx* c) {
   c->partial = c->red = c->step_parts = nullptr;
 }
 
+// Device error word (1: a bounded wait on a TMA copy ran out), kept in red[7].
+int* error_word(lbm_ctx* c) { return reinterpret_cast<int*>(c->red + 7); }
+
+// Reports and clears the error word, given a host copy of red[0..7].
+lbm_status take_device_error(lbm_ctx* c, const double* h) {
+  int word = 0;
+  std::memcpy(&word, h + 7, sizeof(word));
+  if (word == 0) return LBM_OK;
+  cudaMemsetAsync(c->red + 7, 0, sizeof(double), c->stream);
+  return fail(c, LBM_ETIMEOUT,
+              "a bounded wait for a TMA copy in the chemical-potential pass ran out; the "
+              "affected steps are not valid");
+}
+
+// The chemical-potential pass can fetch its halo bricks by TMA when whole bricks tile
+// x and y, the box fits the grid, and phi starts on a 16-byte boundary.
+bool encode_phi_map(lbm_ctx* c) {
+  const lbm::Geometry& g = c->geo;
+  if (!lbm::mu_tma_shape_ok(g) || g.nx < static_cast<int>(lbm::kMuTmaBox[0]) ||
+      g.ny < static_cast<int>(lbm::kMuTmaBox[1]) || g.nz < static_cast<int>(lbm::kMuTmaBox[2]) ||
+      reinterpret_cast<uintptr_t>(c->phi) % 16 != 0)
+    return false;
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(g.nx), static_cast<cuuint64_t>(g.ny),
+                              static_cast<cuuint64_t>(g.nz)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(g.nx) * 4,
+                                 static_cast<cuuint64_t>(g.nx) * g.ny * 4};
+  const cuuint32_t box[3] = {lbm::kMuTmaBox[0], lbm::kMuTmaBox[1], lbm::kMuTmaBox[2]};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return encode(&c->phi_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->phi, dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // Per-warp partials of the fused step sums: 5 doubles per 32 cells.
 size_t step_parts_bytes(long long n) {
   return static_cast<size_t>(lbm::cell_warps(n)) * 5 * sizeof(double);
@@ -267,7 +320,12 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
   const float* src = cur_state(c);
   float* dst = c->params.pattern == LBM_PATTERN_AB ? c->pop[1 - c->cur] : c->pop[c->cur];
   LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->phi, c->geo, pat, c->stream); }));
-  LBM_CK(c, timed(c, 1, [&] { return lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream); }));
+  LBM_CK(c, timed(c, 1, [&] {
+           return c->have_phi_map && c->use_phi_map
+                      ? lbm::launch_mu_tma(c->phi_map, c->phi, c->mu, c->geo, c->ph,
+                                           error_word(c), c->stream)
+                      : lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream);
+         }));
   const bool prev = c->have_prev;
   if (c->vel_kind == LBM_VELOCITY_NONE) {
     LBM_CK(c, timed(c, 2, [&] {
@@ -360,6 +418,8 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   }
   cudaError_t e = cudaMemsetAsync(c->pop[0], 0, state_bytes, c->stream);
   if (e == cudaSuccess && c->pop[1]) e = cudaMemsetAsync(c->pop[1], 0, state_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->red, 0, sizeof(double) * 8, c->stream);
+  c->have_phi_map = encode_phi_map(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     release(c);
@@ -437,9 +497,10 @@ lbm_status lbm_step_reduce(lbm_ctx* c, int n, double* sum_phi, double mom[3]) {
   if (!sum_phi || !mom) return fail(c, LBM_EINVAL, "outputs must not be NULL");
   const lbm_status st = lbm_step_reduce_async(c, n, c->red);
   if (st != LBM_OK) return st;
-  double h[5];
+  double h[8];
   LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (const lbm_status te = take_device_error(c, h); te != LBM_OK) return te;
   *sum_phi = h[0];
   mom[0] = h[1];
   mom[1] = h[2];
@@ -476,11 +537,14 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   if (st == LBM_OK && (mask & LBM_FIELD_P)) st = plane_to_host(c, c->stage + s, p, wide);
   for (int a = 0; a < 3 && st == LBM_OK && (mask & LBM_FIELD_U); ++a)
     st = plane_to_host(c, c->stage + (2 + a) * s, u + a * n, wide);
+  double h[8];
+  if (st == LBM_OK)
+    LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   const cudaError_t es = cudaStreamSynchronize(c->stream);
   dev_free(c, wide);
   if (st != LBM_OK) return st;
   if (es != cudaSuccess) return fail_cuda(c, "lbm_read_fields", es);
-  return LBM_OK;
+  return take_device_error(c, h);
 }
 
 lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
@@ -491,9 +555,10 @@ lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
   LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, phi_now, c->geo, read_pattern(c), c->stream));
   LBM_CK(c, lbm::launch_reduce(cur_state(c), phi_now, c->partial, c->red, c->geo, read_pattern(c),
                                c->vel_kind == LBM_VELOCITY_NONE, c->stream));
-  double h[5];
+  double h[8];
   LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (const lbm_status te = take_device_error(c, h); te != LBM_OK) return te;
   *sum_phi = h[0];
   mom[0] = h[1];
   mom[1] = h[2];
@@ -593,6 +658,10 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
   switch (param) {
     case LBM_TUNE_PREFETCH_COLLIDE: c->geo.prefetch_collide = value; return LBM_OK;
     case LBM_TUNE_PREFETCH_PHI: c->geo.prefetch_phi = value; return LBM_OK;
+    case LBM_TUNE_MU_TMA:
+      if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_MU_TMA takes 0 or 1");
+      c->use_phi_map = value == 1;
+      return LBM_OK;
     default: return fail(c, LBM_EINVAL, "unknown tuning parameter");
   }
 }
@@ -602,6 +671,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
   switch (param) {
     case LBM_TUNE_PREFETCH_COLLIDE: *value = c->geo.prefetch_collide; return LBM_OK;
     case LBM_TUNE_PREFETCH_PHI: *value = c->geo.prefetch_phi; return LBM_OK;
+    case LBM_TUNE_MU_TMA: *value = (c->have_phi_map && c->use_phi_map) ? 1 : 0; return LBM_OK;
     default: return LBM_EINVAL;
   }
 }

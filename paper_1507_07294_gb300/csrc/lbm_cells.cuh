@@ -89,32 +89,17 @@ __device__ __forceinline__ int wrap(int v, int n, int span) {
   return v < 0 ? v + n : v;
 }
 
-// mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2) for brick (bx, by, bz) of the grid;
-// called by all kTX x kTY threads of a block, `tile` in shared memory.  The only barrier
-// is the one after the tile load; threads outside the grid return after it, so a caller
-// that reuses `tile` for another brick must synchronise the block first.
-template <bool D3Q7>
-__device__ __forceinline__ void mu_brick(const float* __restrict__ phi, float* __restrict__ mu,
-                                         const Geometry& geo, const Physics& ph, int bx, int by,
-                                         int bz, float (*tile)[kHY][kHX]) {
-  const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
+// mu of the kTX x kTY columns of brick (x0, y0, z0) from a halo tile already in shared
+// memory: tile[l][i][jj] holds phi at (x0 - XOFF + jj, y0 - 1 + i, z0 - 1 + l) with
+// ghosts and periodic images filled in.  Threads outside the grid return.
+template <bool D3Q7, int HX, int XOFF>
+__device__ __forceinline__ void mu_columns(const float (*tile)[kHY][HX], float* __restrict__ mu,
+                                           const Geometry& geo, const Physics& ph, int x0, int y0,
+                                           int z0) {
   const int lane = threadIdx.x, warp = threadIdx.y;
-  // columns of the halo brick this lane loads: j = lane and, for lanes 0-1, j = 32 + lane
-  const int gx_a = wrap(x0 - 1 + lane, geo.nx, kHX);
-  const int gx_b = wrap(x0 - 1 + kTX + (lane & 1), geo.nx, kHX);
-  for (int r = warp; r < kHZ * kHY; r += kTY) {
-    const int l = r / kHY, i = r - l * kHY;
-    const int gy = wrap(y0 - 1 + i, geo.ny, kHY);
-    const int zz = z0 - 1 + l;
-    const int gz = geo.walls ? min(max(zz, 0), geo.nz - 1) : wrap(zz, geo.nz, kHZ);
-    const float* row = phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx;
-    tile[l][i][lane] = __ldg(row + gx_a);
-    if (lane < 2) tile[l][i][kTX + lane] = __ldg(row + gx_b);
-  }
-  __syncthreads();
   const int x = x0 + lane, y = y0 + warp;
-  if (x >= geo.nx || y >= geo.ny) return;  // no barrier follows in this function
-  const int i = warp + 1, j = lane + 1;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const int i = warp + 1, j = lane + XOFF;
   // per-plane partial sums of column (i, j): centre, faces, diagonals
   auto plane = [&](int l, float& c, float& f, float& d) {
     c = tile[l][i][j];
@@ -139,6 +124,38 @@ __device__ __forceinline__ void mu_brick(const float* __restrict__ phi, float* _
     c0 = c1; f0 = f1; d0 = d1;
     c1 = c2; f1 = f2; d1 = d2;
   }
+}
+
+// Source z of halo plane zz: clamped to the fluid between walls (the stencil ghost is
+// the adjacent node), wrapped when periodic.
+__device__ __forceinline__ int ghost_z(const Geometry& geo, int zz) {
+  return geo.walls ? min(max(zz, 0), geo.nz - 1) : wrap(zz, geo.nz, kHZ);
+}
+
+// mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2) for brick (bx, by, bz) of the grid;
+// called by all kTX x kTY threads of a block, `tile` in shared memory, loaded here with
+// plain loads.  The only barrier is the one after the tile load; threads outside the
+// grid return after it, so a caller that reuses `tile` for another brick must
+// synchronise the block first.
+template <bool D3Q7>
+__device__ __forceinline__ void mu_brick(const float* __restrict__ phi, float* __restrict__ mu,
+                                         const Geometry& geo, const Physics& ph, int bx, int by,
+                                         int bz, float (*tile)[kHY][kHX]) {
+  const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  // columns of the halo brick this lane loads: j = lane and, for lanes 0-1, j = 32 + lane
+  const int gx_a = wrap(x0 - 1 + lane, geo.nx, kHX);
+  const int gx_b = wrap(x0 - 1 + kTX + (lane & 1), geo.nx, kHX);
+  for (int r = warp; r < kHZ * kHY; r += kTY) {
+    const int l = r / kHY, i = r - l * kHY;
+    const int gy = wrap(y0 - 1 + i, geo.ny, kHY);
+    const int gz = ghost_z(geo, z0 - 1 + l);
+    const float* row = phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx;
+    tile[l][i][lane] = __ldg(row + gx_a);
+    if (lane < 2) tile[l][i][kTX + lane] = __ldg(row + gx_b);
+  }
+  __syncthreads();
+  mu_columns<D3Q7, kHX, 1>(tile, mu, geo, ph, x0, y0, z0);
 }
 
 // ------------------------------------------------------ fused stream-collide -------

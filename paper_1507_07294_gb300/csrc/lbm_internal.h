@@ -1,6 +1,7 @@
 // Host-side declarations shared by the C ABI and the kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -20,6 +21,14 @@ cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const
                        int pattern, cudaStream_t st);
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st);
+// The chemical-potential pass with a TMA-fetched halo brick; `map` describes phi as a
+// 3D FP32 tensor (nx, ny, nz) with box (kTX + 8, kTY + 2, kTZ + 2).  Only for grids
+// with mu_tma_shape_ok.  A timed-out copy sets *err to 1.
+cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
+                          const Geometry& geo, const Physics& ph, int* err, cudaStream_t st);
+bool mu_tma_shape_ok(const Geometry& geo);
+// TMA box of the chemical-potential pass: (kTX + 8, kTY + 2, kTZ + 2)
+constexpr unsigned kMuTmaBox[3] = {40, 10, 18};
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
                            const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                            cudaStream_t st);

@@ -13,6 +13,7 @@
 // Every kernel is templated on the population storage pattern and type
 // (lbm_device.cuh); the per-cell bodies live in lbm_cells.cuh, shared with the batched
 // kernels.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_cells.cuh"
@@ -56,6 +57,107 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
                                                  Physics ph) {
   __shared__ float tile[kHZ][kHY][kHX];
   mu_brick<D3Q7>(phi, mu, geo, ph, blockIdx.x, blockIdx.y, blockIdx.z, tile);
+}
+
+// ------------------------------------------------------------- k_mu_tma ---------
+// The same pass with the halo brick fetched by one TMA tensor copy instead of plain
+// loads: box kBX x kHY x kHZ of phi starting at (x0 - 4, y0 - 1, z0 - 1), so the
+// innermost start coordinate stays a multiple of 4 floats (16 bytes); entries outside
+// the grid arrive as zeros and are then replaced, on boundary bricks only, by their
+// periodic image or wall ghost with plain loads.  Needs nx % 32 == 0 and ny % 8 == 0
+// (whole bricks in x and y).  The wait on the copy's mbarrier is bounded: if it runs
+// out, the block sets *err, waits once more (bounded) for its copy, and returns.
+constexpr int kBX = kTX + 8;  // 4 columns either side; the stencil uses columns 3 .. 36
+constexpr unsigned kMuBoxBytes = kBX * kHY * kHZ * 4;
+constexpr long long kMbarSpins = 1 << 22;
+static_assert(kMuTmaBox[0] == kBX && kMuTmaBox[1] == kHY && kMuTmaBox[2] == kHZ,
+              "TMA box of the host descriptor");
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// true once phase `parity` of the mbarrier has completed; false after kMbarSpins polls
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (long long k = 0; k < kMbarSpins; ++k) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <bool D3Q7>
+__global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ CUtensorMap map,
+                                                     const float* __restrict__ phi,
+                                                     float* __restrict__ mu, Geometry geo,
+                                                     Physics ph, int* err) {
+  __shared__ alignas(128) float tile[kHZ][kHY][kBX];
+  __shared__ alignas(8) unsigned long long bar_storage;
+  const unsigned bar = smem_addr(&bar_storage);
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(kMuBoxBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(&tile[0][0][0])),
+        "l"(reinterpret_cast<unsigned long long>(&map)), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1),
+        "r"(bar)
+        : "memory");
+  }
+  if (!__syncthreads_and(mbar_wait(bar, 0))) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mbar_wait(bar, 0);  // let the copy into this block's shared memory land
+    }
+    __syncthreads();
+    return;
+  }
+  // periodic images and wall ghosts of the halo entries outside the grid
+  const int nl = min(kTZ, geo.nz - z0);
+  const bool xlo = x0 == 0, xhi = x0 + kTX >= geo.nx;
+  const bool ylo = y0 == 0, yhi = y0 + kTY >= geo.ny;
+  const bool zlo = z0 == 0, zhi = z0 + nl >= geo.nz;
+  if (xlo || xhi || ylo || yhi || zlo || zhi) {
+    auto fill = [&](int l, int i, int jj) {
+      const int gx = wrap(x0 - 4 + jj, geo.nx, kBX);
+      const int gy = wrap(y0 - 1 + i, geo.ny, kHY);
+      const int gz = ghost_z(geo, z0 - 1 + l);
+      tile[l][i][jj] = __ldg(phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx + gx);
+    };
+    const int nthreads = kTX * kTY;
+    // x faces: columns 3 and kTX + 4 of every row and plane
+    for (int k = tid; k < 2 * kHZ * kHY; k += nthreads) {
+      const int side = k / (kHZ * kHY), r = k - side * kHZ * kHY;
+      if (side == 0 ? xlo : xhi) fill(r / kHY, r % kHY, side == 0 ? 3 : kTX + 4);
+    }
+    // y faces: rows 0 and kTY + 1, columns 3 .. kTX + 4, every plane
+    for (int k = tid; k < 2 * kHZ * (kTX + 2); k += nthreads) {
+      const int side = k / (kHZ * (kTX + 2)), r = k - side * kHZ * (kTX + 2);
+      if (side == 0 ? ylo : yhi) fill(r / (kTX + 2), side == 0 ? 0 : kTY + 1, 3 + r % (kTX + 2));
+    }
+    // z faces: planes 0 and nl + 1, rows 0 .. kTY + 1, columns 3 .. kTX + 4
+    for (int k = tid; k < 2 * kHY * (kTX + 2); k += nthreads) {
+      const int side = k / (kHY * (kTX + 2)), r = k - side * kHY * (kTX + 2);
+      if (side == 0 ? zlo : zhi) fill(side == 0 ? 0 : nl + 1, r / (kTX + 2), 3 + r % (kTX + 2));
+    }
+    __syncthreads();
+  }
+  mu_columns<D3Q7, kBX, 4>(tile, mu, geo, ph, x0, y0, z0);
 }
 
 // -------------------------------------------------------------- k_collide ---------
@@ -415,6 +517,20 @@ cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const
                        int pattern, cudaStream_t st) {
   LBM_DISPATCH(geo, pattern, k_phi, src, phi_ref, phi, geo);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
+                          const Geometry& geo, const Physics& ph, int* err, cudaStream_t st) {
+  const dim3 grid(geo.nx / kTX, geo.ny / kTY, (geo.nz + kTZ - 1) / kTZ);
+  if (ph.d3q7_stencil)
+    k_mu_tma<true><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err);
+  else
+    k_mu_tma<false><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err);
+  return cudaGetLastError();
+}
+
+bool mu_tma_shape_ok(const Geometry& geo) {
+  return geo.nx % kTX == 0 && geo.ny % kTY == 0;
 }
 
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,

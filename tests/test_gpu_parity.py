@@ -321,3 +321,54 @@ def test_read_fields_into_given_buffers(L):
     assert np.shares_memory(got["phi"], bufs["phi"]) and np.shares_memory(got["u"], bufs["u"])
     for k in ("phi", "u", "mu"):
         assert np.array_equal(got[k], ref[k])
+
+
+@pytest.mark.parametrize("shape, walls", [((64, 16, 24), False), ((64, 16, 18), True),
+                                          ((96, 24, 40), True), ((64, 64, 64), False)])
+def test_tma_halo_path_matches_plain_loads(L, shape, walls):
+    """The chemical-potential pass with TMA-fetched halo bricks (grids whose x and y are
+    whole bricks) gives bit-identical states to the plain-load pass, on periodic and
+    walled grids and with a partial last brick in z."""
+    nx, ny, nz = shape
+    if walls:
+        w = I.rayleigh_taylor(W=nx, nz=nz, Re=300.0)
+        w.ny = ny
+        w.phi0 = np.ascontiguousarray(w.phi0[:, :ny, :])
+    else:
+        w = I.droplet(n=nx, R=min(nx, ny, nz) / 3, nx=nx, ny=ny, nz=nz)
+    w = I.perturbed(w, seed=41, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w) as a, L.Solver(w) as b:
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_MU_TMA) == 1
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_MU_TMA, 0)
+        assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_MU_TMA) == 0
+        a.step(7)
+        b.step(7)
+        for x, y in zip(a.state()[:3], b.state()[:3]):
+            assert np.array_equal(x, y)
+        fa, fb = a.fields(L.LBM_FIELD_MU), b.fields(L.LBM_FIELD_MU)
+        assert np.array_equal(fa["mu"], fb["mu"])
+
+
+def test_tma_halo_path_100_steps_against_the_oracle(L):
+    w = I.perturbed(I.rayleigh_taylor(W=64, nz=40, Re=256.0), seed=42, u_amp=0.01, p_amp=1e-4)
+    w.ny = 16
+    w.phi0 = np.ascontiguousarray(w.phi0[:, :16, :])
+    w.u0 = np.ascontiguousarray(w.u0[:, :, :16, :])
+    w.p0 = np.ascontiguousarray(w.p0[:, :16, :])
+    with L.Solver(w) as s:
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_MU_TMA) == 1
+        s.step(100)
+        gf = s.fields()
+    o = _oracle(w)
+    o.step(100)
+    _compare_fields(gf, o.fields(), w.U, p_tol=1e-6)
+
+
+def test_tma_halo_path_only_where_it_applies(L):
+    for shape in ((37, 16, 24), (64, 12, 24), (32, 16, 24), (64, 16, 17)):
+        w = I.droplet(n=16, R=4.0, nx=shape[0], ny=shape[1], nz=shape[2])
+        with L.Solver(w) as s:
+            assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_MU_TMA) == 0, shape
+    with L.Solver(I.droplet(n=16, R=4.0, nx=64, ny=16, nz=18)) as s:
+        with pytest.raises(L.LbmError):
+            L.lbm_set_tuning(s.ctx, L.LBM_TUNE_MU_TMA, 2)
