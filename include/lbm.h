@@ -76,8 +76,8 @@ typedef struct {
  * LBM_PATTERN_AB: two arrays; each step pulls from one and writes the other (176
  *   bytes of populations per cell).  The faster of the two on GB300.
  * LBM_PATTERN_AA: one array updated in place (88 bytes of populations per cell);
- *   alternate steps read and write neighbouring cells' slots, which moves data more
- *   slowly than LBM_PATTERN_AB.  Same results either way, bit for bit. */
+ *   alternate steps read and write neighbouring cells' slots, which costs a few per
+ *   cent of speed against LBM_PATTERN_AB.  Same results either way, bit for bit. */
 #define LBM_PATTERN_AB 0
 #define LBM_PATTERN_AA 1
 
@@ -102,7 +102,8 @@ typedef struct {
 
 /* Device allocator.  alloc returns device memory of at least `bytes` bytes (aligned
  * to 256 bytes) or NULL; free releases it.  Calls happen inside lbm_create,
- * lbm_init_phi and lbm_destroy only. */
+ * lbm_init_phi and lbm_read_fields (one transient staging buffer each) and
+ * lbm_destroy only. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
@@ -122,8 +123,9 @@ typedef struct {
  * a density or viscosity is not positive, or the storage type or pattern is unknown.
  * Device memory per cell: the cell state (22 populations + phi u of the previous
  * step: 100 bytes in FP32, 56 bytes with 16-bit populations; twice for LBM_PATTERN_AB)
- * + phi + mu + 7 staging floats, i.e. 236 bytes (FP32, AB), 136 bytes (FP32, AA) or
- * 148 bytes (16-bit, AB). */
+ * + phi + mu + 7 staging floats + the fused-sum partials, i.e. about 237 bytes (FP32,
+ * AB), 137 bytes (FP32, AA) or 149 bytes (16-bit, AB); lbm_memory_bytes gives the
+ * exact figure. */
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
                       const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out);
 
