@@ -155,7 +155,8 @@ lbm_status lbm_init_phi(lbm_ctx* ctx, const double* phi, const double* u, const 
 lbm_status lbm_set_velocity(lbm_ctx* ctx, int kind, double U, double period);
 
 /* Advance n >= 0 time steps (Eqs. 4 and 20: stream, then collide in moment space with
- * Eqs. 17-18 and 31-32).  Asynchronous on the context's stream. */
+ * Eqs. 17-18 and 31-32).  Asynchronous on the context's stream.  Pairs of steps are
+ * replayed from CUDA graphs captured on first use (see LBM_TUNE_GRAPHS). */
 lbm_status lbm_step(lbm_ctx* ctx, int n);
 
 /* Macroscopic fields at the current time, computed on the device from the current
@@ -221,10 +222,15 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * with TMA tensor copies, 0 uses plain loads; the TMA path exists when nx is a multiple
  * of 32 (and >= 40), ny a multiple of 8 (and >= 10) and nz >= 18, and lbm_get_tuning
  * reports 1 only while it is in use.  Both give identical results.
+ * LBM_TUNE_GRAPHS: 1 (default) lets lbm_step replay pairs of steps as CUDA graphs
+ * (coupled model, after the first step, while not profiling), 0 launches every kernel;
+ * identical results.  Setting any parameter drops the captured graphs (and waits for
+ * the context's stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */
 #define LBM_TUNE_PREFETCH_COLLIDE 0
 #define LBM_TUNE_PREFETCH_PHI 1
 #define LBM_TUNE_MU_TMA 2
+#define LBM_TUNE_GRAPHS 3
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 

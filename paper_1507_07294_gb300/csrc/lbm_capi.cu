@@ -44,6 +44,13 @@ struct lbm_ctx {
   bool have_phi_map = false;
   bool use_phi_map = true;
 
+  // CUDA graphs of two consecutive steps, one per parity of the stored state (which
+  // array is current, or the AA step parity), replayed by lbm_step; captured on first
+  // use, dropped whenever a kernel argument changes (tuning, prescribed velocity)
+  cudaGraphExec_t pair_graph[2] = {nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
+  bool use_graphs = true;
+
   // interface-tracking mode (0: coupled): prescribed velocity kind, amplitude, period
   int vel_kind = 0;
   double vel_U = 0.0, vel_period = 1.0;
@@ -162,7 +169,17 @@ lbm_status validate(const lbm_grid* g, const lbm_params* p) {
   return LBM_OK;
 }
 
+void drop_graphs(lbm_ctx* c) {
+  for (auto& g : c->pair_graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
 void release(lbm_ctx* c) {
+  drop_graphs(c);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  c->capture_stream = nullptr;
   for (auto& list : c->events)
     for (auto& pr : list) {
       cudaEventDestroy(pr.first);
@@ -351,6 +368,53 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
   return LBM_OK;
 }
 
+// Steps of the coupled model with a previous step and no per-kernel timing have fixed
+// kernel arguments, so two of them can be captured once and replayed.
+bool graphs_apply(const lbm_ctx* c) {
+  return c->use_graphs && c->vel_kind == LBM_VELOCITY_NONE && !c->profiling && c->have_prev;
+}
+
+int pair_parity(const lbm_ctx* c) {
+  return c->params.pattern == LBM_PATTERN_AB ? c->cur : (c->odd ? 1 : 0);
+}
+
+// Captures two steps from the current parity into c->pair_graph[parity]; the context's
+// bookkeeping (array parity, step count) is left as it was.
+lbm_status capture_pair(lbm_ctx* c, int parity) {
+  if (!c->capture_stream &&
+      cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(c, LBM_ECUDA, "cudaStreamCreate failed (graph capture)");
+  const int cur = c->cur;
+  const bool odd = c->odd, have_prev = c->have_prev;
+  const long long step = c->step;
+  cudaStream_t stream = c->stream;
+  c->stream = c->capture_stream;
+  cudaError_t e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+  lbm_status st = LBM_OK;
+  if (e == cudaSuccess) {
+    st = step_once(c, nullptr);
+    if (st == LBM_OK) st = step_once(c, nullptr);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = e == cudaSuccess ? cudaStreamEndCapture(c->capture_stream, &graph) : e;
+  c->stream = stream;
+  c->cur = cur;
+  c->odd = odd;
+  c->have_prev = have_prev;
+  c->step = step;
+  if (st != LBM_OK || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != LBM_OK ? st : fail_cuda(c, "graph capture", ec);
+  }
+  e = cudaGraphInstantiate(&c->pair_graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->pair_graph[parity] = nullptr;
+    return fail_cuda(c, "cudaGraphInstantiate", e);
+  }
+  return LBM_OK;
+}
+
 // Whether the last step of lbm_step_reduce can carry the sums (else a separate pass).
 bool fused_sums(const lbm_ctx* c) {
   return c->vel_kind == LBM_VELOCITY_NONE &&
@@ -468,7 +532,25 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
   if (!c) return LBM_EINVAL;
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
   if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
-  for (int it = 0; it < n; ++it) {
+  int it = 0;
+  if (n >= 2 && c->use_graphs && c->vel_kind == LBM_VELOCITY_NONE && !c->profiling &&
+      !c->have_prev) {
+    // the first step after initialisation (d_t(phi u) = 0) is never replayed
+    const lbm_status st = step_once(c, nullptr);
+    if (st != LBM_OK) return st;
+    ++it;
+  }
+  while (n - it >= 2 && graphs_apply(c)) {
+    const int parity = pair_parity(c);
+    if (!c->pair_graph[parity]) {
+      const lbm_status st = capture_pair(c, parity);
+      if (st != LBM_OK) return st;
+    }
+    LBM_CK(c, cudaGraphLaunch(c->pair_graph[parity], c->stream));
+    c->step += 2;  // two steps leave the array parity as it was
+    it += 2;
+  }
+  for (; it < n; ++it) {
     const lbm_status st = step_once(c, nullptr);
     if (st != LBM_OK) return st;
   }
@@ -485,11 +567,8 @@ lbm_status lbm_step_reduce_async(lbm_ctx* c, int n, double* out_dev) {
     const lbm_status st = lbm_step(c, n);
     return st != LBM_OK ? st : lbm_reduce_async(c, out_dev);
   }
-  for (int it = 0; it < n; ++it) {
-    const lbm_status st = step_once(c, it == n - 1 ? out_dev : nullptr);
-    if (st != LBM_OK) return st;
-  }
-  return LBM_OK;
+  const lbm_status st = lbm_step(c, n - 1);
+  return st != LBM_OK ? st : step_once(c, out_dev);
 }
 
 lbm_status lbm_step_reduce(lbm_ctx* c, int n, double* sum_phi, double mom[3]) {
@@ -644,6 +723,8 @@ lbm_status lbm_set_velocity(lbm_ctx* c, int kind, double U, double period) {
   if (!std::isfinite(U)) return fail(c, LBM_EINVAL, "U must be finite");
   if (kind == LBM_VELOCITY_DEFORMATION && !(period > 0 && std::isfinite(period)))
     return fail(c, LBM_EINVAL, "the deformation field needs a period > 0");
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
   c->vel_kind = kind;
   c->vel_U = U;
   c->vel_period = kind == LBM_VELOCITY_DEFORMATION ? period : 1.0;
@@ -656,14 +737,21 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
   if (!c) return LBM_EINVAL;
   if (value < 0) return fail(c, LBM_EINVAL, "tuning values must be >= 0");
   switch (param) {
-    case LBM_TUNE_PREFETCH_COLLIDE: c->geo.prefetch_collide = value; return LBM_OK;
-    case LBM_TUNE_PREFETCH_PHI: c->geo.prefetch_phi = value; return LBM_OK;
+    case LBM_TUNE_PREFETCH_COLLIDE: c->geo.prefetch_collide = value; break;
+    case LBM_TUNE_PREFETCH_PHI: c->geo.prefetch_phi = value; break;
     case LBM_TUNE_MU_TMA:
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_MU_TMA takes 0 or 1");
       c->use_phi_map = value == 1;
-      return LBM_OK;
+      break;
+    case LBM_TUNE_GRAPHS:
+      if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_GRAPHS takes 0 or 1");
+      c->use_graphs = value == 1;
+      break;
     default: return fail(c, LBM_EINVAL, "unknown tuning parameter");
   }
+  cudaStreamSynchronize(c->stream);  // a replay may still be running
+  drop_graphs(c);                    // their kernel arguments may have changed
+  return LBM_OK;
 }
 
 lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
@@ -672,6 +760,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
     case LBM_TUNE_PREFETCH_COLLIDE: *value = c->geo.prefetch_collide; return LBM_OK;
     case LBM_TUNE_PREFETCH_PHI: *value = c->geo.prefetch_phi; return LBM_OK;
     case LBM_TUNE_MU_TMA: *value = (c->have_phi_map && c->use_phi_map) ? 1 : 0; return LBM_OK;
+    case LBM_TUNE_GRAPHS: *value = c->use_graphs ? 1 : 0; return LBM_OK;
     default: return LBM_EINVAL;
   }
 }

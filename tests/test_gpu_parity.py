@@ -372,3 +372,34 @@ def test_tma_halo_path_only_where_it_applies(L):
     with L.Solver(I.droplet(n=16, R=4.0, nx=64, ny=16, nz=18)) as s:
         with pytest.raises(L.LbmError):
             L.lbm_set_tuning(s.ctx, L.LBM_TUNE_MU_TMA, 2)
+
+
+@pytest.mark.parametrize("pattern, storage", [("ab", "fp32"), ("aa", "fp32"), ("ab", "fp16")])
+def test_graph_replay_matches_plain_launches(L, pattern, storage):
+    """lbm_step replays pairs of steps from captured CUDA graphs; the populations must
+    be those of plain launches bit for bit, across odd step counts, a tuning change
+    (which drops the graphs), a checkpoint restore and lbm_step_reduce."""
+    w = I.perturbed(I.rayleigh_taylor(W=64, nz=40, Re=300.0), seed=43, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w, pattern=pattern, storage=storage) as a, \
+            L.Solver(w, pattern=pattern, storage=storage) as b:
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_GRAPHS, 0)
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_GRAPHS) == 1
+        assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_GRAPHS) == 0
+        for s in (a, b):
+            s.step(5)
+            s.step(4)
+        L.lbm_set_tuning(a.ctx, L.LBM_TUNE_PREFETCH_COLLIDE, 100)
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_PREFETCH_COLLIDE, 100)
+        for s in (a, b):
+            s.step(3)
+            L.lbm_step_reduce(s.ctx, 4)
+        assert a.t == b.t == 16
+        sa, sb = a.state(), b.state()
+        for x, y in zip(sa[:3], sb[:3]):
+            assert np.array_equal(x, y)
+        a.set_state(*sa)  # resume from the checkpoint, then replay again
+        b.set_state(*sb)
+        a.step(6)
+        b.step(6)
+        for x, y in zip(a.state()[:3], b.state()[:3]):
+            assert np.array_equal(x, y)
