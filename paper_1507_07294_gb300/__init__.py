@@ -4,18 +4,23 @@ Navier-Stokes lattice, stepped by hand-written CUDA kernels behind a C ABI
 (include/lbm.h).
 
 Submodules:
-    lbm      ctypes binding of liblbm.so (the C entry points, one to one) and Solver
-    inputs   seeded synthetic workloads (grids, parameters, initial fields)
-    _build   nvcc build of liblbm.so
+    lbm          ctypes binding of liblbm.so (the C entry points, one to one), Solver,
+                 Batch
+    serve        continuous-batching request loop over many runs
+    tune         autotuning of the single-run prefetch distances
+    inputs       seeded synthetic workloads (grids, parameters, initial fields)
+    diagnostics  host-side measures of results (Err of Eq. 40, interface fronts)
+    _build       nvcc build of liblbm.so
 
-The binding is imported lazily so that `inputs` can be used without CUDA.
+Submodules are imported lazily so that `inputs` and `diagnostics` can be used without
+CUDA.
 """
 
-__all__ = ["lbm", "inputs"]
+__all__ = ["lbm", "serve", "tune", "inputs", "diagnostics"]
 
 
 def __getattr__(name):
-    if name in ("lbm", "inputs", "_build"):
+    if name in ("lbm", "serve", "tune", "inputs", "diagnostics", "_build"):
         import importlib
         return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)
