@@ -224,13 +224,19 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * reports 1 only while it is in use.  Both give identical results.
  * LBM_TUNE_GRAPHS: 1 (default) lets lbm_step replay pairs of steps as CUDA graphs
  * (coupled model, after the first step, while not profiling), 0 launches every kernel;
- * identical results.  Setting any parameter drops the captured graphs (and waits for
+ * identical results.  LBM_TUNE_TMA_WAIT_POLLS: how many times a block of the TMA
+ * chemical-potential pass polls for its copy before giving up (default 2^22, far more
+ * than a copy takes); a block that gives up sets the error word that the next
+ * lbm_reduce, lbm_step_reduce or lbm_read_fields reports as LBM_ETIMEOUT, and that
+ * step's results are not valid.  0 makes every wait give up at once, which exercises
+ * the failure path.  Setting any parameter drops the captured graphs (and waits for
  * the context's stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */
 #define LBM_TUNE_PREFETCH_COLLIDE 0
 #define LBM_TUNE_PREFETCH_PHI 1
 #define LBM_TUNE_MU_TMA 2
 #define LBM_TUNE_GRAPHS 3
+#define LBM_TUNE_TMA_WAIT_POLLS 4
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 

@@ -43,6 +43,7 @@ struct lbm_ctx {
   CUtensorMap phi_map{};
   bool have_phi_map = false;
   bool use_phi_map = true;
+  long long tma_polls = -1;  // poll budget of the copy's wait; -1: the kernel default
 
   // CUDA graphs of two consecutive steps, one per parity of the stored state (which
   // array is current, or the AA step parity), replayed by lbm_step; captured on first
@@ -340,7 +341,10 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
   LBM_CK(c, timed(c, 1, [&] {
            return c->have_phi_map && c->use_phi_map
                       ? lbm::launch_mu_tma(c->phi_map, c->phi, c->mu, c->geo, c->ph,
-                                           error_word(c), c->stream)
+                                           error_word(c),
+                                           c->tma_polls < 0 ? lbm::mu_tma_default_polls()
+                                                            : c->tma_polls,
+                                           c->stream)
                       : lbm::launch_mu(c->phi, c->mu, c->geo, c->ph, c->stream);
          }));
   const bool prev = c->have_prev;
@@ -747,6 +751,7 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_GRAPHS takes 0 or 1");
       c->use_graphs = value == 1;
       break;
+    case LBM_TUNE_TMA_WAIT_POLLS: c->tma_polls = value; break;
     default: return fail(c, LBM_EINVAL, "unknown tuning parameter");
   }
   cudaStreamSynchronize(c->stream);  // a replay may still be running
@@ -761,6 +766,9 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
     case LBM_TUNE_PREFETCH_PHI: *value = c->geo.prefetch_phi; return LBM_OK;
     case LBM_TUNE_MU_TMA: *value = (c->have_phi_map && c->use_phi_map) ? 1 : 0; return LBM_OK;
     case LBM_TUNE_GRAPHS: *value = c->use_graphs ? 1 : 0; return LBM_OK;
+    case LBM_TUNE_TMA_WAIT_POLLS:
+      *value = static_cast<int>(c->tma_polls < 0 ? lbm::mu_tma_default_polls() : c->tma_polls);
+      return LBM_OK;
     default: return LBM_EINVAL;
   }
 }

@@ -23,9 +23,12 @@ cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Ph
                       cudaStream_t st);
 // The chemical-potential pass with a TMA-fetched halo brick; `map` describes phi as a
 // 3D FP32 tensor (nx, ny, nz) with box (kTX + 8, kTY + 2, kTZ + 2).  Only for grids
-// with mu_tma_shape_ok.  A timed-out copy sets *err to 1.
+// with mu_tma_shape_ok.  A block whose wait for its copy runs out after `polls` polls
+// sets *err to 1 (default budget: mu_tma_default_polls()).
 cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
-                          const Geometry& geo, const Physics& ph, int* err, cudaStream_t st);
+                          const Geometry& geo, const Physics& ph, int* err, long long polls,
+                          cudaStream_t st);
+long long mu_tma_default_polls();
 bool mu_tma_shape_ok(const Geometry& geo);
 // TMA box of the chemical-potential pass: (kTX + 8, kTY + 2, kTZ + 2)
 constexpr unsigned kMuTmaBox[3] = {40, 10, 18};

@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
 // the grid arrive as zeros and are then replaced, on boundary bricks only, by their
 // periodic image or wall ghost with plain loads.  Needs nx % 32 == 0 and ny % 8 == 0
 // (whole bricks in x and y).  The wait on the copy's mbarrier is bounded: if it runs
-// out, the block sets *err, waits once more (bounded) for its copy, and returns.
+// out (after `polls` polls; kMbarSpins by default), the block sets *err, waits once
+// more (bounded) for its copy, and returns.
 constexpr int kBX = kTX + 8;  // 4 columns either side; the stencil uses columns 3 .. 36
 constexpr unsigned kMuBoxBytes = kBX * kHY * kHZ * 4;
 constexpr long long kMbarSpins = 1 << 22;
@@ -77,9 +78,9 @@ __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-// true once phase `parity` of the mbarrier has completed; false after kMbarSpins polls
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (long long k = 0; k < kMbarSpins; ++k) {
+// true once phase `parity` of the mbarrier has completed; false after `polls` polls
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long polls) {
+  for (long long k = 0; k < polls; ++k) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -97,7 +98,7 @@ template <bool D3Q7>
 __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ CUtensorMap map,
                                                      const float* __restrict__ phi,
                                                      float* __restrict__ mu, Geometry geo,
-                                                     Physics ph, int* err) {
+                                                     Physics ph, int* err, long long polls) {
   __shared__ alignas(128) float tile[kHZ][kHY][kBX];
   __shared__ alignas(8) unsigned long long bar_storage;
   const unsigned bar = smem_addr(&bar_storage);
@@ -119,10 +120,10 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
         "r"(bar)
         : "memory");
   }
-  if (!__syncthreads_and(mbar_wait(bar, 0))) {
+  if (!__syncthreads_and(mbar_wait(bar, 0, polls))) {
     if (tid == 0) {
       atomicExch(err, 1);
-      mbar_wait(bar, 0);  // let the copy into this block's shared memory land
+      mbar_wait(bar, 0, kMbarSpins);  // let the copy into this block's shared memory land
     }
     __syncthreads();
     return;
@@ -519,13 +520,16 @@ cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const
   return cudaGetLastError();
 }
 
+long long mu_tma_default_polls() { return kMbarSpins; }
+
 cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
-                          const Geometry& geo, const Physics& ph, int* err, cudaStream_t st) {
+                          const Geometry& geo, const Physics& ph, int* err, long long polls,
+                          cudaStream_t st) {
   const dim3 grid(geo.nx / kTX, geo.ny / kTY, (geo.nz + kTZ - 1) / kTZ);
   if (ph.d3q7_stencil)
-    k_mu_tma<true><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err);
+    k_mu_tma<true><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err, polls);
   else
-    k_mu_tma<false><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err);
+    k_mu_tma<false><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err, polls);
   return cudaGetLastError();
 }
 

@@ -108,3 +108,35 @@ def test_batch_create_reports_a_refused_table(L):
     out = ctypes.c_void_p()
     assert lib.lbm_batch_create(ctypes.byref(a.struct), None, ctypes.byref(out)) == L.LBM_ENOMEM
     assert out.value is None and "batch table" in L.lbm_last_error()
+
+
+def test_tma_wait_budget_runs_out_cleanly(L):
+    """The TMA chemical-potential pass bounds its wait for each copy.  A budget of 0
+    polls makes every block give up at once (it still lets its copy land before
+    exiting): the next reduction reports LBM_ETIMEOUT, the report clears the flag, and
+    the context keeps working."""
+    w = I.perturbed(I.droplet(n=16, R=5.0, nx=64, ny=16, nz=24), seed=51, u_amp=0.01)
+    with L.Solver(w) as s:
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_MU_TMA) == 1
+        default = L.lbm_get_tuning(s.ctx, L.LBM_TUNE_TMA_WAIT_POLLS)
+        assert default > 1000
+        s.step(2)
+        s.reduce()
+        L.lbm_set_tuning(s.ctx, L.LBM_TUNE_TMA_WAIT_POLLS, 0)
+        s.step(1)
+        with pytest.raises(L.LbmError) as e:
+            s.reduce()
+        assert e.value.status == L.LBM_ETIMEOUT and "TMA" in str(e.value)
+        s.reduce()  # reported once, then cleared
+        s.step(1)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_step_reduce(s.ctx, 1)
+        assert e.value.status == L.LBM_ETIMEOUT
+        s.step(1)
+        with pytest.raises(L.LbmError) as e:
+            s.fields(L.LBM_FIELD_PHI)
+        assert e.value.status == L.LBM_ETIMEOUT
+        L.lbm_set_tuning(s.ctx, L.LBM_TUNE_TMA_WAIT_POLLS, default)
+        s.step(3)
+        sp, _ = s.reduce()
+        assert np.isfinite(sp)
