@@ -229,14 +229,20 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * than a copy takes); a block that gives up sets the error word that the next
  * lbm_reduce, lbm_step_reduce or lbm_read_fields reports as LBM_ETIMEOUT, and that
  * step's results are not valid.  0 makes every wait give up at once, which exercises
- * the failure path.  Setting any parameter drops the captured graphs (and waits for
- * the context's stream).
+ * the failure path.
+ * LBM_TUNE_ROWS: 1 (default) lets the order-parameter and stream-collide passes of a
+ * two-array (LBM_PATTERN_AB) run address the pulled populations a whole row of tiles
+ * at a time, which needs nx a multiple of 32 (lbm_get_tuning reports 1 only while it
+ * is in use); 0 keeps the per-cell addressing everywhere.  Identical results.
+ * Setting any parameter drops the captured graphs (and waits for the context's
+ * stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */
 #define LBM_TUNE_PREFETCH_COLLIDE 0
 #define LBM_TUNE_PREFETCH_PHI 1
 #define LBM_TUNE_MU_TMA 2
 #define LBM_TUNE_GRAPHS 3
 #define LBM_TUNE_TMA_WAIT_POLLS 4
+#define LBM_TUNE_ROWS 5
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 

@@ -44,6 +44,7 @@ struct lbm_ctx {
   bool have_phi_map = false;
   bool use_phi_map = true;
   long long tma_polls = -1;  // poll budget of the copy's wait; -1: the kernel default
+  int row_tiles = 0;         // Geometry::row_tiles when LBM_TUNE_ROWS is on
 
   // CUDA graphs of two consecutive steps, one per parity of the stored state (which
   // array is current, or the AA step parity), replayed by lbm_step; captured on first
@@ -129,8 +130,14 @@ lbm::Physics make_physics(const lbm_params& p) {
   ph.eta = static_cast<float>(p.mobility / (p.A * (1.0 / p.sf[1] - 0.5)));
   for (int a = 0; a < 3; ++a) ph.gacc[a] = static_cast<float>(p.g[a]);
   ph.rho_ref = (p.flags & LBM_FLAG_BUOYANCY) ? static_cast<float>(0.5 * (p.rho_l + p.rho_g)) : 0.0f;
-  for (int k = 0; k < 7; ++k) ph.sf[k] = static_cast<float>(p.sf[k]);
-  for (int k = 0; k < 15; ++k) ph.sg[k] = static_cast<float>(p.sg[k]);
+  for (int k = 0; k < 7; ++k) {
+    ph.sf_a[k] = static_cast<float>(p.sf[k] / lbm::norm7(k));
+    ph.sf_b[k] = static_cast<float>((1.0 - 0.5 * p.sf[k]) / lbm::norm7(k));
+  }
+  for (int k = 0; k < 15; ++k) {
+    ph.sg_a[k] = static_cast<float>(p.sg[k] / lbm::norm15(k));
+    ph.sg_b[k] = static_cast<float>((1.0 - 0.5 * p.sg[k]) / lbm::norm15(k));
+  }
   ph.srt_flow = (p.flags & LBM_FLAG_SRT_FLOW) ? 1 : 0;
   ph.d3q7_stencil = (p.flags & LBM_FLAG_D3Q7_STENCIL) ? 1 : 0;
   return ph;
@@ -457,13 +464,21 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   c->geo.storage = params->storage;  // LBM_STORAGE_* numbers match lbm::Storage
   c->geo.div_nx = make_fast_div(static_cast<unsigned>(grid->nx));
   c->geo.div_ny = make_fast_div(static_cast<unsigned>(grid->ny));
+  // whole-tile rows whose planes of tiles span < 2^31 bytes in the widest storage
+  if (grid->nx % lbm::kTile == 0 &&
+      static_cast<long long>(grid->ny) * (grid->nx / lbm::kTile) * lbm::tile_bytes<lbm::kF32>() <
+          (1LL << 31))
+    c->row_tiles = grid->nx / lbm::kTile;
+  c->geo.row_tiles = c->row_tiles;
   // L2 prefetch distances: one wave of resident blocks
   {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
       c->geo.prefetch_collide = sms * lbm::resident_blocks_per_sm(0, c->geo.storage);
-      c->geo.prefetch_phi = sms * lbm::resident_blocks_per_sm(1, c->geo.storage);
+      c->geo.prefetch_phi =
+          sms * lbm::resident_blocks_per_sm(1, c->geo.storage,
+                                            c->geo.row_tiles > 0 && params->pattern == LBM_PATTERN_AB);
     }
   }
   c->ph = make_physics(*params);
@@ -752,6 +767,10 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
       c->use_graphs = value == 1;
       break;
     case LBM_TUNE_TMA_WAIT_POLLS: c->tma_polls = value; break;
+    case LBM_TUNE_ROWS:
+      if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_ROWS takes 0 or 1");
+      c->geo.row_tiles = value == 1 ? c->row_tiles : 0;
+      break;
     default: return fail(c, LBM_EINVAL, "unknown tuning parameter");
   }
   cudaStreamSynchronize(c->stream);  // a replay may still be running
@@ -768,6 +787,9 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
     case LBM_TUNE_GRAPHS: *value = c->use_graphs ? 1 : 0; return LBM_OK;
     case LBM_TUNE_TMA_WAIT_POLLS:
       *value = static_cast<int>(c->tma_polls < 0 ? lbm::mu_tma_default_polls() : c->tma_polls);
+      return LBM_OK;
+    case LBM_TUNE_ROWS:
+      *value = (c->geo.row_tiles > 0 && c->params.pattern == LBM_PATTERN_AB) ? 1 : 0;
       return LBM_OK;
     default: return LBM_EINVAL;
   }

@@ -55,6 +55,65 @@ __device__ __forceinline__ void cell_coords(const Geometry& geo, int idx, int& x
 }
 
 
+// ------------------------------------------------- pull addressing on tile rows -------
+// When every row of the grid is a whole number of tiles (nx a multiple of kTile), the
+// tile of cell (x + dx, y + dy, z + dz) is the own tile moved by whole rows and planes
+// of tiles, and only the x step can leave the tile (lanes 0 and 31).  The byte address
+// of a pulled population is then z[dz] + (x[dx] + y[dy]) + slot offset, the periodic
+// images folded into the per-thread deltas: a few integer operations per distinct
+// source cell instead of a tile mapping per load.  Used for cells off the walls (the
+// bounce-back links keep the general loaders); Geometry::row_tiles is 0 where the
+// layout does not allow it.
+struct RowPull {
+  const char* z[3];  // own slot-0 address moved by dz = -1, 0, +1 planes
+  int x[3], y[3];    // byte deltas of dx, dy = -1, 0, +1
+};
+
+template <int S>
+__device__ __forceinline__ RowPull row_pull(const float* src, const Geometry& geo, int idx,
+                                            int x, int y, int z) {
+  constexpr int EB = static_cast<int>(sizeof(typename Elem<S>::T));
+  constexpr int TB = tile_bytes<S>();
+  constexpr int L = kTile - 1;
+  const int rt = geo.row_tiles, lane = idx & L, row = rt * TB;
+  RowPull r;
+  r.x[1] = 0;
+  r.y[1] = 0;
+  r.x[0] = lane ? -EB : (x ? L * EB - TB : L * EB + (rt - 1) * TB);
+  r.x[2] = lane != L ? EB : (x != geo.nx - 1 ? TB - L * EB : -L * EB - (rt - 1) * TB);
+  r.y[0] = y ? -row : (geo.ny - 1) * row;
+  r.y[2] = y != geo.ny - 1 ? row : -(geo.ny - 1) * row;
+  const long long plane = static_cast<long long>(geo.ny) * row;
+  r.z[1] = reinterpret_cast<const char*>(src) + static_cast<long long>(idx >> kTileShift) * TB +
+           lane * EB;
+  r.z[0] = r.z[1] + (z ? -plane : (geo.nz - 1) * plane);
+  r.z[2] = r.z[1] + (z != geo.nz - 1 ? plane : -(geo.nz - 1) * plane);
+  return r;
+}
+
+// Value of slot SLOT of the cell at offset (DX, DY, DZ).
+template <int S, int SLOT, int DX, int DY, int DZ>
+__device__ __forceinline__ float row_load(const RowPull& r) {
+  typedef typename Elem<S>::T T;
+  const char* p = r.z[DZ + 1] + (r.x[DX + 1] + r.y[DY + 1]);
+  return Elem<S>::get(*reinterpret_cast<const T*>(p + SLOT * kTile * static_cast<int>(sizeof(T))));
+}
+
+// Pull of the pattern-AB loaders (load_f, load_g) for a cell off the walls.
+template <int S>
+__device__ __forceinline__ void row_load_f(const RowPull& r, float f[7]) {
+#define X(I, O, CX, CY, CZ) f[I] = row_load<S, I, -CX, -CY, -CZ>(r);
+  LBM_D3Q7_LIST(X)
+#undef X
+}
+
+template <int S>
+__device__ __forceinline__ void row_load_g(const RowPull& r, float g[15]) {
+#define X(I, O, CX, CY, CZ) g[I] = row_load<S, 7 + I, -CX, -CY, -CZ>(r);
+  LBM_D3Q15_LIST(X)
+#undef X
+}
+
 // ---------------------------------------------------------- order parameter -------
 // phi = sum_i f_i of the streamed populations (Eqs. 13, 16).  With 16-bit storage slot
 // 0 holds f_0 - phi_ref, phi_ref the order parameter of the step that wrote it;
@@ -66,7 +125,10 @@ __device__ __forceinline__ void phi_cell(const float* src, const float* phi_ref,
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
   float f[7];
-  load_f<P, S>(src, idx, nb, f);
+  if (P == kAB && geo.row_tiles && !(nb.wlo || nb.whi))
+    row_load_f<S>(row_pull<S>(src, geo, idx, x, y, z), f);
+  else
+    load_f<P, S>(src, idx, nb, f);
   if (S != kF32) f[0] += phi_ref[idx];
   phi[idx] = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]));
 }
@@ -209,14 +271,20 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   const Nbr nb = make_nbr(geo, x, y, z);
 
   float g[15], f[7], prev[3];
-  load_g<P, S>(src, idx, nb, g);
-  load_f<P, S>(src, idx, nb, f);
+  if (P == kAB && geo.row_tiles && !(nb.wlo || nb.whi)) {
+    const RowPull r = row_pull<S>(src, geo, idx, x, y, z);
+    row_load_g<S>(r, g);
+    row_load_f<S>(r, f);
+  } else {
+    load_g<P, S>(src, idx, nb, g);
+    load_f<P, S>(src, idx, nb, f);
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
 
   const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
   const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
-  const float lambda_visc = 1.0f / (3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
+  const float lambda_visc = __fdividef(1.0f, 3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
   collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
   if (SUMS) {
     typedef Elem<S> E;

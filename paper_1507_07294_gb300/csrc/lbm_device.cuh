@@ -34,6 +34,8 @@ struct Geometry {
   int prefetch_collide;  // L2 prefetch distance of k_collide in blocks (0: none)
   int prefetch_phi;      // same for k_phi
   int storage;           // population storage type (Storage); selects the kernel instance
+  int row_tiles;         // nx / kTile when rows are whole tiles and a plane of tiles spans
+                         // < 2^31 bytes (pull addressing of RowPull), else 0
 };
 
 __device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
@@ -51,13 +53,33 @@ struct Physics {
   float eta, A;      // Eqs. 5, 8, 19
   float gacc[3];     // body acceleration
   float rho_ref;     // G = (rho - rho_ref) g; 0 for the plain weight
-  float sf[7];       // S^f (Eq. 10)
-  float sg[15];      // S^g (Eq. 26), entries 9..13 unused (viscous, per cell)
+  // Relaxation rates divided by the squared norms of the moment rows (norm7, norm15):
+  // sf_a[k] = s_k / |M_k|^2 and sf_b[k] = (1 - s_k / 2) / |M_k|^2 for S^f (Eq. 10);
+  // sg_a, sg_b the same for S^g (Eq. 26), entries 9..13 unused (viscous, per cell).
+  float sf_a[7], sf_b[7];
+  float sg_a[15], sg_b[15];
   int vel_kind;      // 0: coupled; else the prescribed velocity field (VelocityKind)
   float vel_U;       // its amplitude U
   int srt_flow;      // 1: every D3Q15 rate is the viscous one (single relaxation time)
   int d3q7_stencil;  // 1: Eqs. 35-36 with the D3Q7 weights (7-point central differences)
 };
+
+// Squared norms of the rows of M (Eq. 9) and Gamma (Eq. 25): both sets of rows are
+// orthogonal, so M^{-1} = M^T diag(1 / |M_k|^2) and likewise for Gamma.
+//   |M_k|^2     = 7, 2, 2, 2, 42, 12, 4
+//   |Gamma_k|^2 = 15, 18, 360, 10, 40, 10, 40, 10, 40, 12, 4, 8, 8, 8, 8
+__host__ __device__ constexpr float norm7(int k) {
+  return k == 0 ? 7.0f : (k <= 3 ? 2.0f : (k == 4 ? 42.0f : (k == 5 ? 12.0f : 4.0f)));
+}
+__host__ __device__ constexpr float norm15(int k) {
+  return k == 0 ? 15.0f
+       : k == 1 ? 18.0f
+       : k == 2 ? 360.0f
+       : k <= 8 ? ((k & 1) ? 10.0f : 40.0f)
+       : k == 9 ? 12.0f
+       : k == 10 ? 4.0f
+                 : 8.0f;
+}
 
 // Compile-time model variants of the step kernels (bit set): kVarSrtFlow, kVarD3Q7.
 constexpr int kVarSrtFlow = 1;
@@ -447,7 +469,7 @@ __device__ __forceinline__ Macro macroscopic(const Physics& ph, const float g[15
     Fsg[a] = mu * grad_phi[a] + (m.rho - ph.rho_ref) * ph.gacc[a];  // F_s + G
   }
   const float fa = ph.half_drho * ph.mob * lap_mu;  // F_a = fa * u
-  const float inv = 1.0f / (m.rho - 0.5f * fa);
+  const float inv = __fdividef(1.0f, m.rho - 0.5f * fa);
   m.u[0] = (jx + 0.5f * Fsg[0]) * inv;
   m.u[1] = (jy + 0.5f * Fsg[1]) * inv;
   m.u[2] = (jz + 0.5f * Fsg[2]) * inv;
@@ -544,15 +566,15 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
   mT[13] = ux * Yz + uz * Yx;
   mT[14] = 0.0f;
 
-  // Delta_k / |row_k|^2
-  constexpr float inv_n[15] = {1.0f / 15, 1.0f / 18, 1.0f / 360, 1.0f / 10, 1.0f / 40,
-                               1.0f / 10, 1.0f / 40,  1.0f / 10, 1.0f / 40, 1.0f / 12,
-                               1.0f / 4,  1.0f / 8,   1.0f / 8,  1.0f / 8,  1.0f / 8};
+  // Delta_k / |row_k|^2; the fixed rates come divided by the norms
   float a[15];
+  const float keep_visc = 1.0f - 0.5f * lambda_visc;
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
-    const float lam = (SRT || (k >= 9 && k <= 13)) ? lambda_visc : ph.sg[k];
-    a[k] = (lam * (m[k] - meq[k]) - (1.0f - 0.5f * lam) * mT[k]) * inv_n[k];
+    if (SRT || (k >= 9 && k <= 13))
+      a[k] = (lambda_visc * (m[k] - meq[k]) - keep_visc * mT[k]) * (1.0f / norm15(k));
+    else
+      a[k] = ph.sg_a[k] * (m[k] - meq[k]) - ph.sg_b[k] * mT[k];
   }
 
   // back transform: g_i -= sum_k Gamma_ki a_k
@@ -609,13 +631,9 @@ __device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], floa
   const float meq[7] = {phi, phi * u[0], phi * u[1], phi * u[2],
                         6.0f * phi - 21.0f * ph.A * ph.eta * mu, 0.0f, 0.0f};
   const float mR[7] = {0.0f, dphiu[0], dphiu[1], dphiu[2], 0.0f, 0.0f, 0.0f};
-  constexpr float inv_n[7] = {1.0f / 7, 1.0f / 2, 1.0f / 2, 1.0f / 2, 1.0f / 42, 1.0f / 12, 1.0f / 4};
   float b[7];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    const float s = ph.sf[k];
-    b[k] = (s * (m[k] - meq[k]) - (1.0f - 0.5f * s) * mR[k]) * inv_n[k];
-  }
+  for (int k = 0; k < 7; ++k) b[k] = ph.sf_a[k] * (m[k] - meq[k]) - ph.sf_b[k] * mR[k];
   const float e = b[0] - b[4];
   if (SHIFT0)
     f[0] = -(smov + (b[0] + 6.0f * b[4]));

@@ -50,6 +50,93 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
   phi_cell<P, S>(src, phi_ref, phi, geo, idx);
 }
 
+// ------------------------------------------------------------- k_phi_rows ---------
+// k_phi for pattern AB on grids whose rows are whole tiles (Geometry::row_tiles > 0):
+// each warp takes one tile (32 cells of a row) through kPhiRowsK consecutive planes, so
+// the neighbour deltas and the coordinate bookkeeping are computed once per column
+// rather than once per cell, and all loads of the column are issued before the first
+// store (phi_ref may be phi itself: each cell's phi_ref is read before its own write).
+// Block (bx, by): tiles 8 bx .. 8 bx + 7 of a plane, planes kPhiRowsK by onwards.  The
+// sums are phi_cell's, in the same order, so the result is bitwise the same.  Lane 0 of
+// each warp prefetches into L2 the 7 f slots of the tiles that the same warp of block
+// b + geo.prefetch_phi (in launch order) will read.
+constexpr int kPhiRowsK = 4;
+
+template <int S>
+__device__ __forceinline__ void prefetch_rows_ahead(const float* src, const Geometry& geo, int tp) {
+  const int dist = geo.prefetch_phi;
+  if (dist <= 0 || (threadIdx.x & (kTile - 1)) != 0) return;
+  const long long b = blockIdx.x + static_cast<long long>(blockIdx.y) * gridDim.x + dist;
+  const int by = static_cast<int>(b / gridDim.x);
+  if (by >= static_cast<int>(gridDim.y)) return;
+  const int q = static_cast<int>(b - static_cast<long long>(by) * gridDim.x) * (kBlock / kTile) +
+                (threadIdx.x >> kTileShift);
+  if (q >= tp) return;
+  constexpr int bytes = kQ7 * kTile * static_cast<int>(sizeof(typename Elem<S>::T));
+  const int z1 = min(geo.nz, (by + 1) * kPhiRowsK);
+  for (int z = by * kPhiRowsK; z < z1; ++z)
+    prefetch_l2(reinterpret_cast<const char*>(src) + (static_cast<long long>(z) * tp + q) * tile_bytes<S>(),
+                bytes);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_phi_rows(const float* __restrict__ src,
+                                                     const float* phi_ref, float* phi,
+                                                     Geometry geo) {
+  typedef Elem<S> E;
+  typedef typename E::T T;
+  constexpr int EB = static_cast<int>(sizeof(T)), TB = tile_bytes<S>(), L = kTile - 1;
+  constexpr int SL = kTile * EB;  // bytes of one slot of a tile
+  const int tp = geo.plane >> kTileShift;  // tiles per plane
+  prefetch_rows_ahead<S>(src, geo, tp);
+  const int q = blockIdx.x * (kBlock / kTile) + (threadIdx.x >> kTileShift);
+  if (q >= tp) return;
+  const int lane = threadIdx.x & L, rt = geo.row_tiles, row = rt * TB;
+  const int p = q * kTile + lane;  // cell within the plane
+  const int y = fast_div(p, geo.div_nx);
+  const int x = p - y * geo.nx;
+  const int dxm = lane ? -EB : (x ? L * EB - TB : L * EB + (rt - 1) * TB);
+  const int dxp = lane != L ? EB : (x != geo.nx - 1 ? TB - L * EB : -L * EB - (rt - 1) * TB);
+  const int dym = y ? -row : (geo.ny - 1) * row;
+  const int dyp = y != geo.ny - 1 ? row : -(geo.ny - 1) * row;
+  const long long plane_b = static_cast<long long>(tp) * TB;
+  const int z0 = blockIdx.y * kPhiRowsK;
+  const int nk = min(kPhiRowsK, geo.nz - z0);
+  const char* own = reinterpret_cast<const char*>(src) +
+                    (static_cast<long long>(z0) * tp + q) * TB + lane * EB;
+  const int cell0 = z0 * geo.plane + p;
+  auto get = [](const char* a) { return E::get(*reinterpret_cast<const T*>(a)); };
+  float f[kPhiRowsK][7], ref[kPhiRowsK];
+#pragma unroll
+  for (int k = 0; k < kPhiRowsK; ++k) {
+    if (k < nk) {
+      const int z = z0 + k;
+      const char* o = own + k * plane_b;
+      // f_5 comes from z - 1 and f_6 from z + 1; across a wall each is the cell's own
+      // opposite slot (6 and 5), i.e. one slot further and one slot back
+      const char* zm = z > 0 ? o - plane_b : (geo.walls ? o + SL : o + (geo.nz - 1) * plane_b);
+      const char* zp = z < geo.nz - 1 ? o + plane_b
+                                      : (geo.walls ? o - SL : o - (geo.nz - 1) * plane_b);
+      f[k][0] = get(o);
+      f[k][1] = get(o + dxm + 1 * SL);
+      f[k][2] = get(o + dxp + 2 * SL);
+      f[k][3] = get(o + dym + 3 * SL);
+      f[k][4] = get(o + dyp + 4 * SL);
+      f[k][5] = get(zm + 5 * SL);
+      f[k][6] = get(zp + 6 * SL);
+      if (S != kF32) ref[k] = phi_ref[cell0 + k * geo.plane];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPhiRowsK; ++k) {
+    if (k < nk) {
+      if (S != kF32) f[k][0] += ref[k];
+      phi[cell0 + k * geo.plane] =
+          f[k][0] + ((f[k][1] + f[k][2]) + (f[k][3] + f[k][4]) + (f[k][5] + f[k][6]));
+    }
+  }
+}
+
 // ------------------------------------------------------------------- k_mu ---------
 template <bool D3Q7>
 __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
@@ -516,6 +603,18 @@ inline unsigned blocks_for(int n) { return static_cast<unsigned>((n + kBlock - 1
 // ------------------------------------------------------------ host launchers ------
 cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const Geometry& geo,
                        int pattern, cudaStream_t st) {
+  const int tp = geo.plane / kTile;
+  const int chunks = (geo.nz + kPhiRowsK - 1) / kPhiRowsK;
+  if (pattern == kAB && geo.row_tiles > 0 && chunks <= 65535) {
+    const dim3 grid((tp + kBlock / kTile - 1) / (kBlock / kTile), chunks);
+    if (geo.storage == kF16)
+      k_phi_rows<kF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo);
+    else if (geo.storage == kBF16)
+      k_phi_rows<kBF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo);
+    else
+      k_phi_rows<kF32><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo);
+    return cudaGetLastError();
+  }
   LBM_DISPATCH(geo, pattern, k_phi, src, phi_ref, phi, geo);
   return cudaGetLastError();
 }
@@ -642,10 +741,14 @@ cudaError_t launch_widen(const float* in, double* out, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int resident_blocks_per_sm(int kernel, int storage) {
+int resident_blocks_per_sm(int kernel, int storage, bool rows) {
   int blocks = 0;
   cudaError_t e;
-  if (kernel == 0)
+  if (kernel == 1 && rows)
+    e = storage == kF16    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi_rows<kF16>, kBlock, 0)
+        : storage == kBF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi_rows<kBF16>, kBlock, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi_rows<kF32>, kBlock, 0);
+  else if (kernel == 0)
     e = storage == kF16    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kF16>, kBlock, 0)
         : storage == kBF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kBF16>, kBlock, 0)
                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kF32>, kBlock, 0);

@@ -403,3 +403,50 @@ def test_graph_replay_matches_plain_launches(L, pattern, storage):
         b.step(6)
         for x, y in zip(a.state()[:3], b.state()[:3]):
             assert np.array_equal(x, y)
+
+
+ROW_GRIDS = [  # (nx, ny, nz, walls): one and several tiles per row, planes not a multiple
+    (32, 1, 1, False),  # of the order-parameter pass's column, walls on both sides of
+    (32, 3, 5, True),   # a single plane's neighbours, ny = 1 and ny odd
+    (64, 1, 2, True),
+    (64, 8, 9, False),
+    (96, 5, 7, True),
+    (64, 16, 24, False),
+]
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("grid", ROW_GRIDS, ids=lambda g: "x".join(map(str, g[:3])) + ("w" if g[3] else "p"))
+def test_row_addressing_matches_per_cell(L, grid, storage):
+    """The whole-row pull addressing (order-parameter column kernel, row-delta loads in
+    the stream-collide pass) must give the per-cell addressing's state bit for bit."""
+    import dataclasses
+    nx, ny, nz, walls = grid
+    w = I.droplet(n=16, R=min(nx, ny, nz) / 3 + 0.5, nx=nx, ny=ny, nz=nz)
+    if walls:
+        w = dataclasses.replace(w, walls_z=True, g=(0.0, 0.0, -1e-5))
+    w = I.perturbed(w, seed=61, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w, storage=storage) as a, L.Solver(w, storage=storage) as b:
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_ROWS) == 1
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_ROWS, 0)
+        assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_ROWS) == 0
+        for s in (a, b):
+            s.step(7)
+            L.lbm_step_reduce(s.ctx, 2)
+        for x, y in zip(a.state()[:3], b.state()[:3]):
+            assert np.array_equal(x, y)
+        fa, fb = a.fields(), b.fields()
+        assert np.array_equal(fa["phi"], fb["phi"])
+
+
+def test_row_addressing_applicability(L):
+    w = I.droplet(n=16, R=4.0, nx=48, ny=8, nz=8)
+    with L.Solver(w) as s:
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 0  # rows are not whole tiles
+    w = I.droplet(n=16, R=4.0, nx=32, ny=8, nz=8)
+    with L.Solver(w, pattern="aa") as s:
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 0  # in-place pattern
+    with L.Solver(w) as s:
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 1
+        with pytest.raises(L.LbmError):
+            L.lbm_set_tuning(s.ctx, L.LBM_TUNE_ROWS, 2)
