@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kTX* kTY) kb_mu(const BatchTable* __restrict__
 }
 
 template <int S>
-__global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS) kb_collide(
+__global__ void __launch_bounds__(kBlock, collide_min_blocks<S>()) kb_collide(
     const BatchTable* __restrict__ t, int step, int dist) {
   __shared__ RunDesc sd;
   const int nitems = t->total_cells;

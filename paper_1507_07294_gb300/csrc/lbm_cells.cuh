@@ -9,10 +9,14 @@ namespace lbm {
 
 constexpr int kBlock = 256;
 
-// Resident blocks per SM the stream-collide kernels are compiled for (80 registers).
-#ifndef LBM_COLLIDE_MIN_BLOCKS
-#define LBM_COLLIDE_MIN_BLOCKS 3
-#endif
+// Resident blocks per SM the stream-collide kernels are compiled for: 3 (80 registers)
+// with FP32 storage, which is DRAM-bound; 4 (64 registers) with 16-bit storage, which
+// is bound by instruction issue and gains more from the extra warps than it loses to
+// the tighter register budget.
+template <int S>
+constexpr int collide_min_blocks() {
+  return S == kF32 ? 3 : 4;
+}
 
 // Bulk prefetch of [p, p + bytes) into L2 (a hint: no completion to wait for).  p must be
 // 16-byte aligned and bytes a multiple of 16.
@@ -69,25 +73,27 @@ struct RowPull {
   int x[3], y[3];    // byte deltas of dx, dy = -1, 0, +1
 };
 
+// From the neighbour offsets: with whole-tile rows the y and z offsets are multiples of
+// kTile cells, i.e. whole tiles of tile_bytes / kTile bytes per cell; only lanes 0 and
+// 31 step into another tile in x (the previous or next one, or across the periodic
+// image of the row).
 template <int S>
-__device__ __forceinline__ RowPull row_pull(const float* src, const Geometry& geo, int idx,
-                                            int x, int y, int z) {
+__device__ __forceinline__ RowPull row_pull(const float* src, const Nbr& nb, int idx) {
   constexpr int EB = static_cast<int>(sizeof(typename Elem<S>::T));
-  constexpr int TB = tile_bytes<S>();
-  constexpr int L = kTile - 1;
-  const int rt = geo.row_tiles, lane = idx & L, row = rt * TB;
+  constexpr int TB = tile_bytes<S>(), TBC = TB / kTile, L = kTile - 1;
+  static_assert(TB % kTile == 0, "tile bytes per cell");
+  const int lane = idx & L;
   RowPull r;
+  r.x[0] = lane ? -EB : (((nb.xm + 1) >> kTileShift) - 1) * TB + L * EB;
   r.x[1] = 0;
+  r.x[2] = lane != L ? EB : (((nb.xp - 1) >> kTileShift) + 1) * TB - L * EB;
+  r.y[0] = nb.ym * TBC;
   r.y[1] = 0;
-  r.x[0] = lane ? -EB : (x ? L * EB - TB : L * EB + (rt - 1) * TB);
-  r.x[2] = lane != L ? EB : (x != geo.nx - 1 ? TB - L * EB : -L * EB - (rt - 1) * TB);
-  r.y[0] = y ? -row : (geo.ny - 1) * row;
-  r.y[2] = y != geo.ny - 1 ? row : -(geo.ny - 1) * row;
-  const long long plane = static_cast<long long>(geo.ny) * row;
+  r.y[2] = nb.yp * TBC;
   r.z[1] = reinterpret_cast<const char*>(src) + static_cast<long long>(idx >> kTileShift) * TB +
            lane * EB;
-  r.z[0] = r.z[1] + (z ? -plane : (geo.nz - 1) * plane);
-  r.z[2] = r.z[1] + (z != geo.nz - 1 ? plane : -(geo.nz - 1) * plane);
+  r.z[0] = r.z[1] + static_cast<long long>(nb.zm) * TBC;
+  r.z[2] = r.z[1] + static_cast<long long>(nb.zp) * TBC;
   return r;
 }
 
@@ -126,7 +132,7 @@ __device__ __forceinline__ void phi_cell(const float* src, const float* phi_ref,
   const Nbr nb = make_nbr(geo, x, y, z);
   float f[7];
   if (P == kAB && geo.row_tiles && !(nb.wlo || nb.whi))
-    row_load_f<S>(row_pull<S>(src, geo, idx, x, y, z), f);
+    row_load_f<S>(row_pull<S>(src, nb, idx), f);
   else
     load_f<P, S>(src, idx, nb, f);
   if (S != kF32) f[0] += phi_ref[idx];
@@ -272,7 +278,7 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
 
   float g[15], f[7], prev[3];
   if (P == kAB && geo.row_tiles && !(nb.wlo || nb.whi)) {
-    const RowPull r = row_pull<S>(src, geo, idx, x, y, z);
+    const RowPull r = row_pull<S>(src, nb, idx);
     row_load_g<S>(r, g);
     row_load_f<S>(r, f);
   } else {
@@ -283,9 +289,10 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
 
   const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
-  const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
+  const Moments15 mo = moments15(g);
+  const Macro M = macroscopic(ph, mo, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   const float lambda_visc = __fdividef(1.0f, 3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
-  collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, M, lambda_visc);
+  collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, mo, M, lambda_visc);
   if (SUMS) {
     typedef Elem<S> E;
     float v[15];

@@ -348,6 +348,22 @@ __device__ __forceinline__ void place_g(float* a, int idx, const Nbr& nb, const 
 }
 
 // ---------------------------------------------------------------------------------
+// Paired FP32 arithmetic.  Blackwell issues two FP32 additions, products or fused
+// multiply-adds as one instruction (__fadd2_rn, __fmul2_rn, __ffma2_rn), each lane
+// rounded exactly like the scalar operation.  The per-cell transforms below pair
+// operations of the same form on independent values (mirrored population pairs, x and
+// y components), which cuts the instructions the stream-collide kernel issues.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as b * (-1) + a: the product is exact, so each lane rounds like a - b
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------------
 // Isotropic difference schemes on the 15-point D3Q15 stencil (Eqs. 35-36 with the
 // flow-lattice weights 1/9 (faces), 1/72 (corners) and c_s^2 = 1/3):
 //   grad chi = 1/3 (face differences) + 1/24 (corner differences)
@@ -390,17 +406,29 @@ __device__ __forceinline__ void stencil_grad7(const Stencil& s, float g[3]) {
 }
 
 __device__ __forceinline__ float stencil_lap(const Stencil& s) {
-  const float faces = (s.xm + s.xp) + (s.ym + s.yp) + (s.zm + s.zp);
-  const float corners = ((s.k[0] + s.k[1]) + (s.k[2] + s.k[3])) + ((s.k[4] + s.k[5]) + (s.k[6] + s.k[7]));
+  const float2 fxy = padd(pr(s.xm, s.ym), pr(s.xp, s.yp));
+  const float faces = (fxy.x + fxy.y) + (s.zm + s.zp);
+  // (k0 + k1 + k4 + k5, k2 + k3 + k6 + k7)
+  const float2 c = padd(padd(pr(s.k[0], s.k[2]), pr(s.k[1], s.k[3])),
+                        padd(pr(s.k[4], s.k[6]), pr(s.k[5], s.k[7])));
+  const float corners = c.x + c.y;
   return (2.0f / 3.0f) * (faces - 6.0f * s.c) + (1.0f / 12.0f) * (corners - 8.0f * s.c);
 }
 
+// Corner sums sum_corners c_a chi: the x differences and x sums of the four (y, z)
+// rows of corners, paired as (y-, y+) per z plane, then combined along y and z.
 __device__ __forceinline__ void stencil_grad(const Stencil& s, float g[3]) {
-  const float kx = (s.k[1] - s.k[0]) + (s.k[3] - s.k[2]) + (s.k[5] - s.k[4]) + (s.k[7] - s.k[6]);
-  const float ky = (s.k[2] - s.k[0]) + (s.k[3] - s.k[1]) + (s.k[6] - s.k[4]) + (s.k[7] - s.k[5]);
-  const float kz = (s.k[4] - s.k[0]) + (s.k[5] - s.k[1]) + (s.k[6] - s.k[2]) + (s.k[7] - s.k[3]);
-  g[0] = (1.0f / 3.0f) * (s.xp - s.xm) + (1.0f / 24.0f) * kx;
-  g[1] = (1.0f / 3.0f) * (s.yp - s.ym) + (1.0f / 24.0f) * ky;
+  const float2 lo0 = pr(s.k[0], s.k[2]), hi0 = pr(s.k[1], s.k[3]);  // z- plane: x-, x+
+  const float2 lo1 = pr(s.k[4], s.k[6]), hi1 = pr(s.k[5], s.k[7]);  // z+ plane
+  const float2 dx = padd(psub(hi0, lo0), psub(hi1, lo1));  // x differences, (y-, y+)
+  const float2 sx0 = padd(hi0, lo0), sx1 = padd(hi1, lo1);  // x sums, (y-, y+) per plane
+  const float2 sy = padd(sx0, sx1);                          // (y- total, y+ total)
+  const float2 sz = psub(sx1, sx0);                          // z+ minus z-, (y-, y+)
+  const float kx = dx.x + dx.y, ky = sy.y - sy.x, kz = sz.x + sz.y;
+  const float2 gxy = pfma(pr(1.0f / 24.0f, 1.0f / 24.0f), pr(kx, ky),
+                          pmul(pr(1.0f / 3.0f, 1.0f / 3.0f), psub(pr(s.xp, s.yp), pr(s.xm, s.ym))));
+  g[0] = gxy.x;
+  g[1] = gxy.y;
   g[2] = (1.0f / 3.0f) * (s.zp - s.zm) + (1.0f / 24.0f) * kz;
 }
 
@@ -450,18 +478,58 @@ struct Macro {
   float F[3];  // F_s + F_a + G
 };
 
-// Eqs. 14, 29, 30 and the forces of Eq. 28.
-__device__ __forceinline__ Macro macroscopic(const Physics& ph, const float g[15], float phi,
+// Moments of the D3Q15 populations (rows of Gamma, Eq. 25) and sum_{i != 0} g_i.
+struct Moments15 {
+  float m[15];
+  float moving;
+};
+
+// The opposite pairs are taken as butterflies, two at a time: (1, 3) with (2, 4) gives
+// the x and y axes; the corners pair by c_y, (7, 9) | (8, 10) for c_y = +1 and
+// (11, 13) | (12, 14) for c_y = -1, and two more butterfly levels give their moments.
+__device__ __forceinline__ Moments15 moments15(const float g[15]) {
+  Moments15 r;
+  const float2 A = pr(g[1], g[3]), B = pr(g[2], g[4]);
+  const float2 s_xy = padd(A, B), d_xy = psub(A, B);  // (sx, sy), (dx, dy)
+  const float sz = g[5] + g[6], dz = g[5] - g[6];
+  const float2 c1 = pr(g[7], g[9]), c2 = pr(g[8], g[10]);
+  const float2 c3 = pr(g[11], g[13]), c4 = pr(g[12], g[14]);
+  const float2 sa_ = padd(c1, c2), da = psub(c1, c2);  // (s7, s9), (d7, d9)
+  const float2 sb = padd(c3, c4), db = psub(c3, c4);   // (s11, s13), (d11, d13)
+  const float2 sp = padd(sa_, sb), sm = psub(sa_, sb);  // (s7 + s11, s9 + s13), (s7 - s11, s9 - s13)
+  const float2 dp = padd(da, db), dm = psub(da, db);    // likewise for d
+  const float C = sp.x + sp.y;                          // sum over the 8 corners
+  const float2 Cxy = pr(dp.x + dp.y, dm.x + dm.y);      // sum c_x g, sum c_y g over corners
+  const float Cz = dp.x - dp.y;
+  const float sa = s_xy.x + s_xy.y + sz;
+  r.moving = sa + C;
+  r.m[0] = g[0] + sa + C;
+  r.m[1] = -2.0f * g[0] - sa + C;
+  r.m[2] = 16.0f * g[0] - 4.0f * sa + C;
+  const float2 m35 = padd(d_xy, Cxy), m46 = pfma(pr(-4.0f, -4.0f), d_xy, Cxy);
+  r.m[3] = m35.x;
+  r.m[4] = m46.x;
+  r.m[5] = m35.y;
+  r.m[6] = m46.y;
+  r.m[7] = dz + Cz;
+  r.m[8] = -4.0f * dz + Cz;
+  r.m[9] = 2.0f * s_xy.x - s_xy.y - sz;
+  r.m[10] = s_xy.y - sz;
+  r.m[11] = sm.x + sm.y;  // c_x c_y
+  r.m[12] = sm.x - sm.y;  // c_y c_z
+  r.m[13] = sp.x - sp.y;  // c_x c_z
+  r.m[14] = dm.x - dm.y;  // c_x c_y c_z
+  return r;
+}
+
+// Eqs. 14, 29, 30 and the forces of Eq. 28, from the moments of the populations.
+__device__ __forceinline__ Macro macroscopic(const Physics& ph, const Moments15& mo, float phi,
                                              float mu, const float grad_phi[3], float lap_mu) {
   Macro m;
   m.rho = ph.rho_g + (1.0f + phi) * ph.half_drho;
   // lattice momentum sum_i c_i g_i and sum_{i != 0} g_i
-  const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12], d13 = g[13] - g[14];
-  const float jx = (g[1] - g[2]) + ((d7 + d9) + (d11 + d13));
-  const float jy = (g[3] - g[4]) + ((d7 + d9) - (d11 + d13));
-  const float jz = (g[5] - g[6]) + ((d7 - d9) + (d11 - d13));
-  const float sum_moving = ((g[1] + g[2]) + (g[3] + g[4]) + (g[5] + g[6])) +
-                           (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14])));
+  const float jx = mo.m[3], jy = mo.m[5], jz = mo.m[7];
+  const float sum_moving = mo.moving;
   float Fsg[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -490,37 +558,9 @@ __device__ __forceinline__ Macro macroscopic(const Physics& ph, const float g[15
 // Gamma^{-1} = Gamma^T diag(1/|row_k|^2), |row|^2 = 15,18,360,10,40,10,40,10,40,12,4,8,8,8,8.
 // ---------------------------------------------------------------------------------
 template <bool SRT = false>
-__device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], const Macro& M,
-                                              float lambda_visc) {
-  // forward transform (rows as polynomials of c; see Eq. 25)
-  const float sx = g[1] + g[2], dx = g[1] - g[2];
-  const float sy = g[3] + g[4], dy = g[3] - g[4];
-  const float sz = g[5] + g[6], dz = g[5] - g[6];
-  const float s7 = g[7] + g[8], d7 = g[7] - g[8];     // +-(1, 1, 1)
-  const float s9 = g[9] + g[10], d9 = g[9] - g[10];   // +-(1, 1,-1)
-  const float s11 = g[11] + g[12], d11 = g[11] - g[12]; // +-(1,-1, 1)
-  const float s13 = g[13] + g[14], d13 = g[13] - g[14]; // +-(1,-1,-1)
-  const float sa = sx + sy + sz;
-  const float C = (s7 + s9) + (s11 + s13);
-  const float Cx = (d7 + d9) + (d11 + d13);
-  const float Cy = (d7 + d9) - (d11 + d13);
-  const float Cz = (d7 - d9) + (d11 - d13);
-  float m[15];
-  m[0] = g[0] + sa + C;
-  m[1] = -2.0f * g[0] - sa + C;
-  m[2] = 16.0f * g[0] - 4.0f * sa + C;
-  m[3] = dx + Cx;
-  m[4] = -4.0f * dx + Cx;
-  m[5] = dy + Cy;
-  m[6] = -4.0f * dy + Cy;
-  m[7] = dz + Cz;
-  m[8] = -4.0f * dz + Cz;
-  m[9] = 2.0f * sx - sy - sz;
-  m[10] = sy - sz;
-  m[11] = (s7 + s9) - (s11 + s13);
-  m[12] = (s7 - s9) - (s11 - s13);
-  m[13] = (s7 - s9) + (s11 - s13);
-  m[14] = (d7 - d9) - (d11 - d13);
+__device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], const Moments15& mo,
+                                              const Macro& M, float lambda_visc) {
+  const float* m = mo.m;
 
   // equilibrium moments, Eq. 31 (c = 1)
   const float rho = M.rho, p = M.p, ux = M.u[0], uy = M.u[1], uz = M.u[2];
@@ -581,30 +621,43 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
   const float e_axis = a[0] - a[1] - 4.0f * a[2];
   g[0] -= a[0] - 2.0f * a[1] + 16.0f * a[2];
   {
-    const float ox = a[3] - 4.0f * a[4], ex = e_axis + 2.0f * a[9];
-    g[1] -= ex + ox;
-    g[2] -= ex - ox;
-    const float oy = a[5] - 4.0f * a[6], ey = e_axis - a[9] + a[10];
-    g[3] -= ey + oy;
-    g[4] -= ey - oy;
+    // axis v: g(+v) -= e_v + o_v, g(-v) -= e_v - o_v; x and y paired, then z
+    const float2 o_xy = pfma(pr(-4.0f, -4.0f), pr(a[4], a[6]), pr(a[3], a[5]));
+    const float2 e_xy = pr(e_axis + 2.0f * a[9], e_axis - a[9] + a[10]);
+    const float2 gp = psub(pr(g[1], g[3]), padd(e_xy, o_xy));
+    const float2 gm = psub(pr(g[2], g[4]), psub(e_xy, o_xy));
+    g[1] = gp.x;
+    g[3] = gp.y;
+    g[2] = gm.x;
+    g[4] = gm.y;
     const float oz = a[7] - 4.0f * a[8], ez = e_axis - a[9] - a[10];
     g[5] -= ez + oz;
     g[6] -= ez - oz;
   }
   {
+    // corner v = (vx, vy, vz): g(+v) -= even + odd, g(-v) -= even - odd, with
+    // even = e0 + vx vy a11 + vy vz a12 + vx vz a13 and odd = vx px + vy py + vz pz +
+    // vx vy vz a14.  The corners with vx = 1 pair as (vz = +1, vz = -1): (7, 9) for
+    // vy = +1, (11, 13) for vy = -1; then
+    //   even = (e0 + vz a13) + vy (a11 + vz a12),  odd = (px + vz pz) + vy (py + vz a14)
     const float e0 = a[0] + a[1] + a[2];
     const float px = a[3] + a[4], py = a[5] + a[6], pz = a[7] + a[8];
-    // corner v = (vx, vy, vz): even part e0 + vx vy a11 + vy vz a12 + vx vz a13,
-    // odd part vx px + vy py + vz pz + vx vy vz a14; g(+v) -= even + odd, g(-v) -= even - odd
-    float e, o;
-    e = e0 + a[11] + a[12] + a[13]; o = px + py + pz + a[14];   // (1, 1, 1)
-    g[7] -= e + o; g[8] -= e - o;
-    e = e0 + a[11] - a[12] - a[13]; o = px + py - pz - a[14];   // (1, 1,-1)
-    g[9] -= e + o; g[10] -= e - o;
-    e = e0 - a[11] - a[12] + a[13]; o = px - py + pz - a[14];   // (1,-1, 1)
-    g[11] -= e + o; g[12] -= e - o;
-    e = e0 - a[11] + a[12] - a[13]; o = px - py - pz + a[14];   // (1,-1,-1)
-    g[13] -= e + o; g[14] -= e - o;
+    const float2 P = pr(e0 + a[13], e0 - a[13]), Q = pr(a[11] + a[12], a[11] - a[12]);
+    const float2 R = pr(px + pz, px - pz), T = pr(py + a[14], py - a[14]);
+    const float2 e_up = padd(P, Q), e_dn = psub(P, Q);  // vy = +1, -1
+    const float2 o_up = padd(R, T), o_dn = psub(R, T);
+    const float2 g79 = psub(pr(g[7], g[9]), padd(e_up, o_up));
+    const float2 g810 = psub(pr(g[8], g[10]), psub(e_up, o_up));
+    const float2 g1113 = psub(pr(g[11], g[13]), padd(e_dn, o_dn));
+    const float2 g1214 = psub(pr(g[12], g[14]), psub(e_dn, o_dn));
+    g[7] = g79.x;
+    g[9] = g79.y;
+    g[8] = g810.x;
+    g[10] = g810.y;
+    g[11] = g1113.x;
+    g[13] = g1113.y;
+    g[12] = g1214.x;
+    g[14] = g1214.y;
   }
 }
 
@@ -618,16 +671,19 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
 template <bool SHIFT0 = false>
 __device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], float phi, float mu,
                                              const float u[3], const float dphiu[3]) {
-  const float sx = f[1] + f[2], sy = f[3] + f[4], sz = f[5] + f[6];
-  const float smov = sx + sy + sz;
+  // x and y opposite pairs as paired butterflies, (1, 3) with (2, 4)
+  const float2 fp = pr(f[1], f[3]), fm = pr(f[2], f[4]);
+  const float2 s_xy = padd(fp, fm), d_xy = psub(fp, fm);
+  const float sz = f[5] + f[6];
+  const float smov = s_xy.x + s_xy.y + sz;
   float m[7];
   m[0] = SHIFT0 ? phi : f[0] + smov;
-  m[1] = f[1] - f[2];
-  m[2] = f[3] - f[4];
+  m[1] = d_xy.x;
+  m[2] = d_xy.y;
   m[3] = f[5] - f[6];
   m[4] = SHIFT0 ? 6.0f * phi - 7.0f * smov : 6.0f * f[0] - smov;
-  m[5] = 2.0f * sx - sy - sz;
-  m[6] = sy - sz;
+  m[5] = 2.0f * s_xy.x - s_xy.y - sz;
+  m[6] = s_xy.y - sz;
   const float meq[7] = {phi, phi * u[0], phi * u[1], phi * u[2],
                         6.0f * phi - 21.0f * ph.A * ph.eta * mu, 0.0f, 0.0f};
   const float mR[7] = {0.0f, dphiu[0], dphiu[1], dphiu[2], 0.0f, 0.0f, 0.0f};
@@ -639,12 +695,12 @@ __device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], floa
     f[0] = -(smov + (b[0] + 6.0f * b[4]));
   else
     f[0] -= b[0] + 6.0f * b[4];
-  const float ex = e + 2.0f * b[5];
-  f[1] -= ex + b[1];
-  f[2] -= ex - b[1];
-  const float ey = e - b[5] + b[6];
-  f[3] -= ey + b[2];
-  f[4] -= ey - b[2];
+  const float2 e_xy = pr(e + 2.0f * b[5], e - b[5] + b[6]), b12 = pr(b[1], b[2]);
+  const float2 up = psub(fp, padd(e_xy, b12)), dn = psub(fm, psub(e_xy, b12));
+  f[1] = up.x;
+  f[3] = up.y;
+  f[2] = dn.x;
+  f[4] = dn.y;
   const float ez = e - b[5] - b[6];
   f[5] -= ez + b[3];
   f[6] -= ez - b[3];

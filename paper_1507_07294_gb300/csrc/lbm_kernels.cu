@@ -58,19 +58,18 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
 // store (phi_ref may be phi itself: each cell's phi_ref is read before its own write).
 // Block (bx, by): tiles 8 bx .. 8 bx + 7 of a plane, planes kPhiRowsK by onwards.  The
 // sums are phi_cell's, in the same order, so the result is bitwise the same.  Lane 0 of
-// each warp prefetches into L2 the 7 f slots of the tiles that the same warp of block
-// b + geo.prefetch_phi (in launch order) will read.
+// each warp prefetches into L2 the 7 f slots of the tiles that the same warp of the
+// block `ahead` rows of blocks further (blockIdx.y + ahead) will read; the launcher
+// turns the prefetch distance geo.prefetch_phi, in blocks, into rows of blocks.
 constexpr int kPhiRowsK = 4;
 
 template <int S>
-__device__ __forceinline__ void prefetch_rows_ahead(const float* src, const Geometry& geo, int tp) {
-  const int dist = geo.prefetch_phi;
-  if (dist <= 0 || (threadIdx.x & (kTile - 1)) != 0) return;
-  const long long b = blockIdx.x + static_cast<long long>(blockIdx.y) * gridDim.x + dist;
-  const int by = static_cast<int>(b / gridDim.x);
+__device__ __forceinline__ void prefetch_rows_ahead(const float* src, const Geometry& geo, int tp,
+                                                    int ahead) {
+  if (ahead <= 0 || (threadIdx.x & (kTile - 1)) != 0) return;
+  const int by = static_cast<int>(blockIdx.y) + ahead;
   if (by >= static_cast<int>(gridDim.y)) return;
-  const int q = static_cast<int>(b - static_cast<long long>(by) * gridDim.x) * (kBlock / kTile) +
-                (threadIdx.x >> kTileShift);
+  const int q = blockIdx.x * (kBlock / kTile) + (threadIdx.x >> kTileShift);
   if (q >= tp) return;
   constexpr int bytes = kQ7 * kTile * static_cast<int>(sizeof(typename Elem<S>::T));
   const int z1 = min(geo.nz, (by + 1) * kPhiRowsK);
@@ -82,13 +81,13 @@ __device__ __forceinline__ void prefetch_rows_ahead(const float* src, const Geom
 template <int S>
 __global__ void __launch_bounds__(kBlock) k_phi_rows(const float* __restrict__ src,
                                                      const float* phi_ref, float* phi,
-                                                     Geometry geo) {
+                                                     Geometry geo, int ahead) {
   typedef Elem<S> E;
   typedef typename E::T T;
   constexpr int EB = static_cast<int>(sizeof(T)), TB = tile_bytes<S>(), L = kTile - 1;
   constexpr int SL = kTile * EB;  // bytes of one slot of a tile
   const int tp = geo.plane >> kTileShift;  // tiles per plane
-  prefetch_rows_ahead<S>(src, geo, tp);
+  prefetch_rows_ahead<S>(src, geo, tp, ahead);
   const int q = blockIdx.x * (kBlock / kTile) + (threadIdx.x >> kTileShift);
   if (q >= tp) return;
   const int lane = threadIdx.x & L, rt = geo.row_tiles, row = rt * TB;
@@ -251,7 +250,7 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
 // -------------------------------------------------------------- k_collide ---------
 
 template <int P, int VAR, int S>
-__global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
     k_collide(const float* src, float* dst, const float* __restrict__ phi,
               const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev) {
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
@@ -267,7 +266,7 @@ __global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
 // small fraction of FP32, and no block barrier holds finished warps back); everything
 // above in FP64, in a fixed order.
 template <int P, int S>
-__global__ void __launch_bounds__(kBlock, LBM_COLLIDE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
     k_collide_sums(const float* src, float* dst, const float* __restrict__ phi,
                    const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev,
                    double* __restrict__ parts) {
@@ -353,7 +352,7 @@ __global__ void __launch_bounds__(kBlock) k_fields(const float* __restrict__ src
                                           : cell_stencils<false>(phi, mu, idx, nb);
   float g[15];
   load_g<P, S>(src, idx, nb, g);
-  const Macro M = macroscopic(ph, g, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
+  const Macro M = macroscopic(ph, moments15(g), cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   out[0 * s + idx] = M.rho;
   out[1 * s + idx] = M.p;
   out[2 * s + idx] = M.u[0];
@@ -607,12 +606,15 @@ cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const
   const int chunks = (geo.nz + kPhiRowsK - 1) / kPhiRowsK;
   if (pattern == kAB && geo.row_tiles > 0 && chunks <= 65535) {
     const dim3 grid((tp + kBlock / kTile - 1) / (kBlock / kTile), chunks);
+    const int ahead = geo.prefetch_phi > 0
+                          ? static_cast<int>((geo.prefetch_phi + grid.x - 1) / grid.x)
+                          : 0;
     if (geo.storage == kF16)
-      k_phi_rows<kF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo);
+      k_phi_rows<kF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
     else if (geo.storage == kBF16)
-      k_phi_rows<kBF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo);
+      k_phi_rows<kBF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
     else
-      k_phi_rows<kF32><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo);
+      k_phi_rows<kF32><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
     return cudaGetLastError();
   }
   LBM_DISPATCH(geo, pattern, k_phi, src, phi_ref, phi, geo);
