@@ -163,10 +163,6 @@ __device__ __forceinline__ size_t phiu_index(int i, int a) {
          (i & (kTile - 1));
 }
 
-// FP32 layout helpers (slot of cell i as a float index), used where the storage type
-// is FP32 by construction.
-__device__ __forceinline__ size_t tile_base(int i) { return tile_floats<kF32>(i) + (i & (kTile - 1)); }
-
 // ---------------------------------------------------------------------------------
 // Neighbour offsets of one cell.  x and y wrap; z wraps or, between walls, the
 // stencil ghost of an out-of-range node is the node itself (offset 0).

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
 // each warp prefetches into L2 the 7 f slots of the tiles that the same warp of the
 // block `ahead` rows of blocks further (blockIdx.y + ahead) will read; the launcher
 // turns the prefetch distance geo.prefetch_phi, in blocks, into rows of blocks.
-constexpr int kPhiRowsK = 4;
+constexpr int kPhiRowsK = 2;
 
 template <int S>
 __device__ __forceinline__ void prefetch_rows_ahead(const float* src, const Geometry& geo, int tp,
