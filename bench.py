@@ -10,8 +10,9 @@ Printed JSON line (rank 0):
   value      MLUPS (million cell updates per second) over all ranks, device-timed with
              CUDA events around exactly --steps steps; inputs resident in HBM.
   e2e        the same metric through the public C ABI with host buffers: pinned-host
-             phi0 uploaded by lbm_init_phi, every step taken by lbm_step_reduce (the step
-             plus the FP64 mass and momentum of its result, read back to the host),
+             phi0 uploaded by lbm_init_phi, every step taken by lbm_step_reduce_async
+             (the step plus the FP64 mass, momentum and non-finite count of its result,
+             copied to pinned host memory and checked there, two steps in flight),
              lbm_read_fields (phi, u, p) at the end.
   roofline   the fused stream-collide kernel: algorithmic bytes per launch / its mean
              CUDA-event duration, against the measured HBM copy bandwidth.
@@ -416,11 +417,32 @@ def run_ours(args):
         # page-locked result buffers, allocated once like a server's I/O buffers
         outs = {k: torch.empty(c * cells, dtype=torch.float64, pin_memory=True).numpy()
                 for k, c in (("phi", 1), ("u", 3), ("p", 1))}
+        # every step's FP64 sums (sum phi, momentum, count of non-finite cells) go to the
+        # host through two pinned slots: step k is enqueued once the sums of step k - 2
+        # have arrived and been checked, so the GPU never waits for the host
+        sums_dev = torch.zeros((2, 8), dtype=torch.float64, device=device)
+        sums_host = torch.zeros((2, 8), dtype=torch.float64, pin_memory=True)
+        arrived = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def check_sums(slot):
+            arrived[slot].synchronize()
+            v = sums_host[slot].numpy()
+            if v[4] != 0 or not np.isfinite(v[:4]).all():
+                raise RuntimeError(f"e2e run diverged: sums {v[:5]}")
+
         barrier()
         t0 = time.perf_counter()
         L.lbm_init_phi(ctx, phi_host)
-        for _ in range(args.steps):
-            L.lbm_step_reduce(ctx, 1)  # the step and the FP64 sums of its result
+        for k in range(args.steps):
+            slot = k & 1
+            if k >= 2:
+                check_sums(slot)
+            L.lbm_step_reduce_async(ctx, 1, sums_dev[slot].data_ptr())  # step + its sums
+            with torch.cuda.stream(stream):
+                sums_host[slot].copy_(sums_dev[slot], non_blocking=True)
+                arrived[slot].record(stream)
+        for k in range(max(0, args.steps - 2), args.steps):
+            check_sums(k & 1)
         out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P, out=outs)
         barrier()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
