@@ -3,8 +3,10 @@
 //
 // One time step is three grid passes; the data dependency radius is 2 (lap mu at x
 // needs mu at x +- c_i, which needs phi at x +- 2 c_i):
-//   k_phi      phi = sum_i f_i of the streamed populations (Eqs. 13, 16)
-//   k_mu       mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2, Eq. 36)
+//   k_phi      phi = sum_i f_i of the streamed populations (Eqs. 13, 16); k_phi_rows
+//              is the same pass for grids whose rows are whole tiles
+//   k_mu       mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2, Eq. 36); k_mu_tma
+//              fetches its halo bricks with TMA tensor copies
 //   k_collide  fused: pull f and g, stencils of phi and mu, forces, u and p, both MRT
 //              collisions, d_t(phi u), store f+ and g+ (Eqs. 14-34)
 // plus k_collide_sums (k_collide that also sums the state it writes, for
