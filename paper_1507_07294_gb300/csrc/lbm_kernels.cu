@@ -282,16 +282,22 @@ __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
     bad = !(isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3]));
   }
   const unsigned nbad = __popc(__ballot_sync(0xffffffffu, bad));
+  // Warp sums of the four values with 6 shuffles instead of 20: across lane bit 4 a lane
+  // keeps two values and hands its partner the other two, across bit 3 one of those, so
+  // that lane l then carries value 2 (l >> 4 & 1) + (l >> 3 & 1) over 4 lanes; three
+  // butterfly levels over bits 2..0 complete each sum in its group of 8 lanes.
+  const unsigned lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8;
+  const float keep0 = b4 ? s[2] : s[0], keep1 = b4 ? s[3] : s[1];
+  const float give0 = b4 ? s[0] : s[2], give1 = b4 ? s[1] : s[3];
+  const float a0 = keep0 + __shfl_xor_sync(0xffffffffu, give0, 16);
+  const float a1 = keep1 + __shfl_xor_sync(0xffffffffu, give1, 16);
+  float v = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-  if ((threadIdx.x & 31) == 0) {
-    double* out = parts + static_cast<size_t>(idx >> 5) * 5;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = static_cast<double>(s[k]);
-    out[4] = static_cast<double>(nbad);
-  }
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  double* out = parts + static_cast<size_t>(idx >> 5) * 5;
+  if ((lane & 7) == 0) out[lane >> 3] = static_cast<double>(v);
+  if (lane == 0) out[4] = static_cast<double>(nbad);
 }
 
 // ------------------------------------------------------------------ k_che ---------
