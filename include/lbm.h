@@ -230,10 +230,11 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * lbm_reduce, lbm_step_reduce or lbm_read_fields reports as LBM_ETIMEOUT, and that
  * step's results are not valid.  0 makes every wait give up at once, which exercises
  * the failure path.
- * LBM_TUNE_ROWS: 1 (default) lets the order-parameter and stream-collide passes of a
- * two-array (LBM_PATTERN_AB) run address the pulled populations a whole row of tiles
- * at a time, which needs nx a multiple of 32 (lbm_get_tuning reports 1 only while it
- * is in use); 0 keeps the per-cell addressing everywhere.  Identical results.
+ * LBM_TUNE_ROWS: 1 (default) lets the order-parameter and stream-collide passes address
+ * the populations they exchange with neighbouring cells a whole row of tiles at a time
+ * (the pulls of LBM_PATTERN_AB, the reads and writes of the odd LBM_PATTERN_AA steps),
+ * which needs nx a multiple of 32 (lbm_get_tuning reports 1 only while it is in use);
+ * 0 keeps the per-cell addressing everywhere.  Identical results.
  * Setting any parameter drops the captured graphs (and waits for the context's
  * stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */

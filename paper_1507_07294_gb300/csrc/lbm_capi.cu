@@ -789,7 +789,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
       *value = static_cast<int>(c->tma_polls < 0 ? lbm::mu_tma_default_polls() : c->tma_polls);
       return LBM_OK;
     case LBM_TUNE_ROWS:
-      *value = (c->geo.row_tiles > 0 && c->params.pattern == LBM_PATTERN_AB) ? 1 : 0;
+      *value = c->geo.row_tiles > 0 ? 1 : 0;
       return LBM_OK;
     default: return LBM_EINVAL;
   }

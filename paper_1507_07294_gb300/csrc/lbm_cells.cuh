@@ -66,8 +66,9 @@ __device__ __forceinline__ void cell_coords(const Geometry& geo, int idx, int& x
 // of a pulled population is then z[dz] + (x[dx] + y[dy]) + slot offset, the periodic
 // images folded into the per-thread deltas: a few integer operations per distinct
 // source cell instead of a tile mapping per load.  Used for cells off the walls (the
-// bounce-back links keep the general loaders); Geometry::row_tiles is 0 where the
-// layout does not allow it.
+// bounce-back links keep the general loaders), by the two-array pulls and by the odd
+// steps of the in-place pattern; Geometry::row_tiles is 0 where the layout does not
+// allow it.
 struct RowPull {
   const char* z[3];  // own slot-0 address moved by dz = -1, 0, +1 planes
   int x[3], y[3];    // byte deltas of dx, dy = -1, 0, +1
@@ -105,19 +106,51 @@ __device__ __forceinline__ float row_load(const RowPull& r) {
   return Elem<S>::get(*reinterpret_cast<const T*>(p + SLOT * kTile * static_cast<int>(sizeof(T))));
 }
 
-// Pull of the pattern-AB loaders (load_f, load_g) for a cell off the walls.
-template <int S>
+// Store v into slot SLOT of the cell at offset (DX, DY, DZ).
+template <int S, int SLOT, int DX, int DY, int DZ>
+__device__ __forceinline__ void row_store(const RowPull& r, float v) {
+  typedef typename Elem<S>::T T;
+  char* p = const_cast<char*>(r.z[DZ + 1]) + (r.x[DX + 1] + r.y[DY + 1]);
+  *reinterpret_cast<T*>(p + SLOT * kTile * static_cast<int>(sizeof(T))) = Elem<S>::put(v);
+}
+
+// The loaders of pattern P (load_f, load_g) for a cell off the walls: AB pulls slot i
+// of x - c_i; the odd step of the in-place pattern reads slot opp(i) of x - c_i.
+template <int P, int S>
 __device__ __forceinline__ void row_load_f(const RowPull& r, float f[7]) {
-#define X(I, O, CX, CY, CZ) f[I] = row_load<S, I, -CX, -CY, -CZ>(r);
+#define X(I, O, CX, CY, CZ) f[I] = row_load<S, P == kAAOdd ? O : I, -CX, -CY, -CZ>(r);
+  LBM_D3Q7_LIST(X)
+#undef X
+}
+
+template <int P, int S>
+__device__ __forceinline__ void row_load_g(const RowPull& r, float g[15]) {
+#define X(I, O, CX, CY, CZ) g[I] = row_load<S, 7 + (P == kAAOdd ? O : I), -CX, -CY, -CZ>(r);
+  LBM_D3Q15_LIST(X)
+#undef X
+}
+
+// The odd step of the in-place pattern writes f_i+ to slot i of x + c_i (store_f,
+// store_g for a cell off the walls).
+template <int S>
+__device__ __forceinline__ void row_store_f_odd(const RowPull& r, const float f[7]) {
+#define X(I, O, CX, CY, CZ) row_store<S, I, CX, CY, CZ>(r, f[I]);
   LBM_D3Q7_LIST(X)
 #undef X
 }
 
 template <int S>
-__device__ __forceinline__ void row_load_g(const RowPull& r, float g[15]) {
-#define X(I, O, CX, CY, CZ) g[I] = row_load<S, 7 + I, -CX, -CY, -CZ>(r);
+__device__ __forceinline__ void row_store_g_odd(const RowPull& r, const float g[15]) {
+#define X(I, O, CX, CY, CZ) row_store<S, 7 + I, CX, CY, CZ>(r, g[I]);
   LBM_D3Q15_LIST(X)
 #undef X
+}
+
+// Whether pattern P addresses this cell's neighbours by rows of tiles: two-array pulls
+// and the odd in-place step, on grids of whole-tile rows, off the walls.
+template <int P>
+__device__ __forceinline__ bool use_rows(const Geometry& geo, const Nbr& nb) {
+  return (P == kAB || P == kAAOdd) && geo.row_tiles && !(nb.wlo || nb.whi);
 }
 
 // ---------------------------------------------------------- order parameter -------
@@ -131,8 +164,8 @@ __device__ __forceinline__ void phi_cell(const float* src, const float* phi_ref,
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
   float f[7];
-  if (P == kAB && geo.row_tiles && !(nb.wlo || nb.whi))
-    row_load_f<S>(row_pull<S>(src, nb, idx), f);
+  if (use_rows<P>(geo, nb))
+    row_load_f<P, S>(row_pull<S>(src, nb, idx), f);
   else
     load_f<P, S>(src, idx, nb, f);
   if (S != kF32) f[0] += phi_ref[idx];
@@ -277,10 +310,10 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   const Nbr nb = make_nbr(geo, x, y, z);
 
   float g[15], f[7], prev[3];
-  if (P == kAB && geo.row_tiles && !(nb.wlo || nb.whi)) {
+  if (use_rows<P>(geo, nb)) {
     const RowPull r = row_pull<S>(src, nb, idx);
-    row_load_g<S>(r, g);
-    row_load_f<S>(r, f);
+    row_load_g<P, S>(r, g);
+    row_load_f<P, S>(r, f);
   } else {
     load_g<P, S>(src, idx, nb, g);
     load_f<P, S>(src, idx, nb, f);
@@ -318,7 +351,10 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
     sums[2] = jy;
     sums[3] = jz;
   }
-  store_g<P, S>(dst, idx, nb, g);
+  if (P == kAAOdd && use_rows<P>(geo, nb))
+    row_store_g_odd<S>(row_pull<S>(dst, nb, idx), g);
+  else
+    store_g<P, S>(dst, idx, nb, g);
 
   // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
   float dphiu[3];
@@ -338,7 +374,10 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
                     (E::get(E::put(f[3])) + E::get(E::put(f[4]))) +
                     (E::get(E::put(f[5])) + E::get(E::put(f[6]))));
   }
-  store_f<P, S>(dst, idx, nb, f);
+  if (P == kAAOdd && use_rows<P>(geo, nb))
+    row_store_f_odd<S>(row_pull<S>(dst, nb, idx), f);
+  else
+    store_f<P, S>(dst, idx, nb, f);
 }
 
 }  // namespace lbm

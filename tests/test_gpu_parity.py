@@ -415,18 +415,21 @@ ROW_GRIDS = [  # (nx, ny, nz, walls): one and several tiles per row, planes not 
 ]
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("pattern, storage", [("ab", "fp32"), ("ab", "fp16"), ("ab", "bf16"),
+                                              ("aa", "fp32")])
 @pytest.mark.parametrize("grid", ROW_GRIDS, ids=lambda g: "x".join(map(str, g[:3])) + ("w" if g[3] else "p"))
-def test_row_addressing_matches_per_cell(L, grid, storage):
-    """The whole-row pull addressing (order-parameter column kernel, row-delta loads in
-    the stream-collide pass) must give the per-cell addressing's state bit for bit."""
+def test_row_addressing_matches_per_cell(L, grid, pattern, storage):
+    """The whole-row addressing (order-parameter column kernel and row-delta loads of
+    the two-array pattern; row-delta loads and stores of the odd in-place steps) must
+    give the per-cell addressing's state bit for bit."""
     import dataclasses
     nx, ny, nz, walls = grid
     w = I.droplet(n=16, R=min(nx, ny, nz) / 3 + 0.5, nx=nx, ny=ny, nz=nz)
     if walls:
         w = dataclasses.replace(w, walls_z=True, g=(0.0, 0.0, -1e-5))
     w = I.perturbed(w, seed=61, u_amp=0.01, p_amp=1e-3)
-    with L.Solver(w, storage=storage) as a, L.Solver(w, storage=storage) as b:
+    with L.Solver(w, pattern=pattern, storage=storage) as a, \
+            L.Solver(w, pattern=pattern, storage=storage) as b:
         assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_ROWS) == 1
         L.lbm_set_tuning(b.ctx, L.LBM_TUNE_ROWS, 0)
         assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_ROWS) == 0
@@ -445,7 +448,7 @@ def test_row_addressing_applicability(L):
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 0  # rows are not whole tiles
     w = I.droplet(n=16, R=4.0, nx=32, ny=8, nz=8)
     with L.Solver(w, pattern="aa") as s:
-        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 0  # in-place pattern
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 1  # the odd in-place steps
     with L.Solver(w) as s:
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 1
         with pytest.raises(L.LbmError):
