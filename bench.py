@@ -454,11 +454,19 @@ def run_ours(args):
 
     # ---- reduced-precision storage variants (same workload and step count) ------
     variants = None
+    pattern_variants = None
     if not args.no_variants and args.storage == "fp32":
         solver.close()
         variants = {}
-        for storage in ("fp16", "bf16"):
-            vs = L.Solver(w, stream=stream.cuda_stream, storage=storage)
+        pattern_variants = {}
+        runs = [("fp16", "ab", "fp16"), ("bf16", "ab", "bf16")]
+        if args.pattern == "ab":
+            runs.append(("aa", "aa", "fp32"))  # in place: half the state memory
+        for name, pattern, storage in runs:
+            wide_v = storage == "fp32"
+            cb = COLLIDE_BYTES_PER_CELL if wide_v else COLLIDE_BYTES_PER_CELL_16
+            sb = STEP_BYTES_PER_CELL if wide_v else STEP_BYTES_PER_CELL_16
+            vs = L.Solver(w, stream=stream.cuda_stream, pattern=pattern, storage=storage)
             vs.step(args.warmup)
             if not args.no_tune:
                 tune.autotune(vs.ctx)
@@ -473,14 +481,21 @@ def run_ours(args):
             vms = max_over_ranks(v0.elapsed_time(v1))
             cms, cn = L.lbm_profile_read(vs.ctx, L.KERNEL_COLLIDE)
             cmean = cms / max(cn, 1)
-            variants[storage] = {
+            entry = {
                 "value": round(aggregate_mlups(cells, args.steps, world, vms * 1e-3), 3),
                 "unit": UNIT, "ms_per_step": round(vms / args.steps, 5),
                 "speedup_vs_fp32": round(elapsed_ms / vms, 3),
                 "k_collide_ms": round(cmean, 5),
-                "k_collide_bytes_per_cell": COLLIDE_BYTES_PER_CELL_16,
-                "k_collide_frac": round(COLLIDE_BYTES_PER_CELL_16 * cells / (cmean * 1e-3) / 1e9 / peak, 4),
-                "step_bytes_per_cell": STEP_BYTES_PER_CELL_16}
+                "k_collide_bytes_per_cell": cb,
+                "k_collide_frac": round(cb * cells / (cmean * 1e-3) / 1e9 / peak, 4),
+                "step_bytes_per_cell": sb}
+            if pattern == "aa":
+                for key, pat in (("context_gb", pattern), ("context_gb_ab", "ab")):
+                    grid_p, params_p = L.params_from_workload(w, pat, storage)
+                    entry[key] = round(L.lbm_memory_bytes(grid_p, params_p) / 1e9, 2)
+                pattern_variants[name] = entry
+            else:
+                variants[name] = entry
             vs.close()
 
     if variants is None:
@@ -513,7 +528,7 @@ def run_ours(args):
                                        (elapsed_ms * 1e-3) / 1e9 / peak, 4),
                 "kernels": kernels,
                 "tuning": {k: v["value"] for k, v in tuning.items()} if tuning else None,
-                "storage_variants": variants,
+                "storage_variants": variants, "pattern_variants": pattern_variants,
                 "serving": serving,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
                 "gpu_launches": 3 * args.steps,
