@@ -67,17 +67,18 @@ typedef struct {
 /* Storage types of the populations for lbm_params.storage.  Arithmetic is FP32 in
  * every case; phi u, phi and mu stay FP32.  With FP16/BF16 the population f_0 is kept as
  * f_0 - phi (phi of the step that wrote it), since f_0 ~ phi ~ +-1 would lose ~3 decimal
- * digits in 16 bits.  16-bit storage needs LBM_PATTERN_AB. */
+ * digits in 16 bits.  Every storage type works with both patterns. */
 #define LBM_STORAGE_FP32 0
 #define LBM_STORAGE_FP16 1
 #define LBM_STORAGE_BF16 2
 
 /* Population storage patterns for lbm_params.pattern.
  * LBM_PATTERN_AB: two arrays; each step pulls from one and writes the other (176
- *   bytes of populations per cell).  The faster of the two on GB300.
- * LBM_PATTERN_AA: one array updated in place (88 bytes of populations per cell);
- *   alternate steps read and write neighbouring cells' slots, which costs a few per
- *   cent of speed against LBM_PATTERN_AB.  Same results either way, bit for bit. */
+ *   bytes of FP32 populations per cell).  The batched calls (lbm_batch_*) take these
+ *   runs only.
+ * LBM_PATTERN_AA: one array updated in place (88 bytes of FP32 populations per cell);
+ *   alternate steps read and write neighbouring cells' slots.  On GB300 it runs as
+ *   fast as LBM_PATTERN_AB.  Same results either way, bit for bit. */
 #define LBM_PATTERN_AB 0
 #define LBM_PATTERN_AA 1
 

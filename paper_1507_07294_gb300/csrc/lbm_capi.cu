@@ -172,8 +172,6 @@ lbm_status validate(const lbm_grid* g, const lbm_params* p) {
     return fail(nullptr, LBM_EINVAL, "unknown storage type");
   if (p->pattern != LBM_PATTERN_AB && p->pattern != LBM_PATTERN_AA)
     return fail(nullptr, LBM_EINVAL, "unknown population pattern");
-  if (p->storage != LBM_STORAGE_FP32 && p->pattern != LBM_PATTERN_AB)
-    return fail(nullptr, LBM_EINVAL, "16-bit storage needs LBM_PATTERN_AB");
   return LBM_OK;
 }
 

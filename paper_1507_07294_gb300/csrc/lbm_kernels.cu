@@ -590,19 +590,25 @@ inline unsigned blocks_for(int n) { return static_cast<unsigned>((n + kBlock - 1
 
 // Host-side dispatch of a kernel template over the pattern (FP32 storage) or the
 // 16-bit storage types (pattern AB only).
-#define LBM_DISPATCH(geo, pattern, KERNEL, ...)                                          \
-  do {                                                                                   \
-    const unsigned blocks_ = blocks_for((geo).n);                                         \
-    if ((geo).storage == kF16)                                                           \
-      KERNEL<kAB, kF16><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                       \
-    else if ((geo).storage == kBF16)                                                     \
-      KERNEL<kAB, kBF16><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                      \
-    else if ((pattern) == kAB)                                                           \
-      KERNEL<kAB, kF32><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                       \
-    else if ((pattern) == kAAEven)                                                       \
-      KERNEL<kAAEven, kF32><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                   \
-    else                                                                                 \
-      KERNEL<kAAOdd, kF32><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);                    \
+#define LBM_DISPATCH_P(pattern, KERNEL, S, ...)                        \
+  {                                                                    \
+    if ((pattern) == kAB)                                              \
+      KERNEL<kAB, S><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);         \
+    else if ((pattern) == kAAEven)                                     \
+      KERNEL<kAAEven, S><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);     \
+    else                                                               \
+      KERNEL<kAAOdd, S><<<blocks_, kBlock, 0, st>>>(__VA_ARGS__);      \
+  }
+
+#define LBM_DISPATCH(geo, pattern, KERNEL, ...)                        \
+  do {                                                                 \
+    const unsigned blocks_ = blocks_for((geo).n);                      \
+    if ((geo).storage == kF16)                                         \
+      LBM_DISPATCH_P(pattern, KERNEL, kF16, __VA_ARGS__)               \
+    else if ((geo).storage == kBF16)                                   \
+      LBM_DISPATCH_P(pattern, KERNEL, kBF16, __VA_ARGS__)              \
+    else                                                               \
+      LBM_DISPATCH_P(pattern, KERNEL, kF32, __VA_ARGS__)               \
   } while (0)
 
 }  // namespace
@@ -661,16 +667,22 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
                      const Geometry& geo, const Physics& ph, int pattern, int prev,
                      cudaStream_t st) {
   const unsigned blocks = blocks_for(geo.n);
+#define LBM_COLLIDE_P(S)                                                                    \
+  {                                                                                         \
+    if (pattern == kAB)                                                                     \
+      k_collide<kAB, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);     \
+    else if (pattern == kAAEven)                                                            \
+      k_collide<kAAEven, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev); \
+    else                                                                                    \
+      k_collide<kAAOdd, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);  \
+  }
   if (geo.storage == kF16)
-    k_collide<kAB, VAR, kF16><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+    LBM_COLLIDE_P(kF16)
   else if (geo.storage == kBF16)
-    k_collide<kAB, VAR, kBF16><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
-  else if (pattern == kAB)
-    k_collide<kAB, VAR, kF32><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
-  else if (pattern == kAAEven)
-    k_collide<kAAEven, VAR, kF32><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+    LBM_COLLIDE_P(kBF16)
   else
-    k_collide<kAAOdd, VAR, kF32><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);
+    LBM_COLLIDE_P(kF32)
+#undef LBM_COLLIDE_P
 }
 
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
@@ -776,16 +788,13 @@ cudaError_t launch_reduce(const float* src, const float* phi, double* partial, d
                           const Geometry& geo, int pattern, bool with_g, cudaStream_t st) {
   const int parts = reduce_parts(geo);
   const int wg = with_g ? 1 : 0;
+  const unsigned blocks_ = static_cast<unsigned>(parts);
   if (geo.storage == kF16)
-    k_reduce_partial<kAB, kF16><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+    LBM_DISPATCH_P(pattern, k_reduce_partial, kF16, src, phi, partial, geo, wg)
   else if (geo.storage == kBF16)
-    k_reduce_partial<kAB, kBF16><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
-  else if (pattern == kAB)
-    k_reduce_partial<kAB, kF32><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
-  else if (pattern == kAAEven)
-    k_reduce_partial<kAAEven, kF32><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+    LBM_DISPATCH_P(pattern, k_reduce_partial, kBF16, src, phi, partial, geo, wg)
   else
-    k_reduce_partial<kAAOdd, kF32><<<parts, kBlock, 0, st>>>(src, phi, partial, geo, wg);
+    LBM_DISPATCH_P(pattern, k_reduce_partial, kF32, src, phi, partial, geo, wg)
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_final<<<1, kBlock, 0, st>>>(partial, parts, out);

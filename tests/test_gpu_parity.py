@@ -374,7 +374,8 @@ def test_tma_halo_path_only_where_it_applies(L):
             L.lbm_set_tuning(s.ctx, L.LBM_TUNE_MU_TMA, 2)
 
 
-@pytest.mark.parametrize("pattern, storage", [("ab", "fp32"), ("aa", "fp32"), ("ab", "fp16")])
+@pytest.mark.parametrize("pattern, storage", [("ab", "fp32"), ("aa", "fp32"), ("ab", "fp16"),
+                                              ("aa", "bf16")])
 def test_graph_replay_matches_plain_launches(L, pattern, storage):
     """lbm_step replays pairs of steps from captured CUDA graphs; the populations must
     be those of plain launches bit for bit, across odd step counts, a tuning change
@@ -416,7 +417,7 @@ ROW_GRIDS = [  # (nx, ny, nz, walls): one and several tiles per row, planes not 
 
 
 @pytest.mark.parametrize("pattern, storage", [("ab", "fp32"), ("ab", "fp16"), ("ab", "bf16"),
-                                              ("aa", "fp32")])
+                                              ("aa", "fp32"), ("aa", "fp16")])
 @pytest.mark.parametrize("grid", ROW_GRIDS, ids=lambda g: "x".join(map(str, g[:3])) + ("w" if g[3] else "p"))
 def test_row_addressing_matches_per_cell(L, grid, pattern, storage):
     """The whole-row addressing (order-parameter column kernel and row-delta loads of

@@ -65,19 +65,38 @@ def test_reduced_precision_errors_100_steps(L, storage, case):
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
-def test_reduced_precision_resume_is_bit_exact(L, storage):
+@pytest.mark.parametrize("other", ["ab", "aa"])
+def test_reduced_precision_resume_is_bit_exact(L, storage, other):
+    """A 16-bit run resumed from its checkpoint, in either pattern, continues bit for
+    bit; the in-place pattern stores exactly the two-array pattern's values."""
     w = I.perturbed(I.rayleigh_taylor(W=16, nz=24, Re=100.0), seed=19, u_amp=0.01, p_amp=1e-3)
     with L.Solver(w, storage=storage) as a:
         a.step(3)
         st = a.state()
         a.step(5)
         ref = a.state()
-    with L.Solver(w, init=False, storage=storage) as b:
+    with L.Solver(w, init=False, pattern=other, storage=storage) as b:
         b.set_state(*st)
         b.step(5)
         got = b.state()
     for x, y in zip(ref[:3], got[:3]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_precision_in_place_matches_two_arrays(L, storage):
+    """Same 16-bit storage, both patterns, from the initial condition: identical states
+    after odd and even step counts (the in-place layout swaps slots every step)."""
+    w = I.perturbed(I.droplet(n=16, R=5.0, nx=32, ny=16, nz=12), seed=23, u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w, storage=storage) as a, L.Solver(w, pattern="aa", storage=storage) as b:
+        for n in (3, 4):
+            a.step(n)
+            b.step(n)
+            for x, y in zip(a.state()[:3], b.state()[:3]):
+                assert np.array_equal(x, y)
+        fa, fb = a.fields(), b.fields()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])

@@ -38,8 +38,6 @@ def _tol(w):
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 @pytest.mark.parametrize("case", ["walled", "periodic"])
 def test_fused_sums_match_the_separate_reduction(L, case, pattern, storage):
-    if storage != "fp32" and pattern == "aa":
-        pytest.skip("16-bit storage runs pattern AB only")
     w = _walled() if case == "walled" else _periodic()
     with L.Solver(w, pattern=pattern, storage=storage) as s:
         s.step(2)
@@ -66,8 +64,6 @@ def test_fused_sums_match_the_oracle(L):
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 @pytest.mark.parametrize("pattern", ["ab", "aa"])
 def test_fused_step_stores_what_lbm_step_stores(L, pattern, storage):
-    if storage != "fp32" and pattern == "aa":
-        pytest.skip("16-bit storage runs pattern AB only")
     w = _walled()
     with L.Solver(w, pattern=pattern, storage=storage) as a, \
             L.Solver(w, pattern=pattern, storage=storage) as b:
