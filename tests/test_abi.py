@@ -64,7 +64,6 @@ def _good():
     (lambda g, p: p.sf.__setitem__(2, 1.3), "s_1 = s_2 = s_3"),
     (lambda g, p: p.sg.__setitem__(0, 0.0), "sg rates"),
     (lambda g, p: setattr(p, "storage", 7), "storage"),
-    (lambda g, p: (setattr(p, "storage", 1), setattr(p, "pattern", 1)), "16-bit storage"),
     (lambda g, p: setattr(p, "pattern", 2), "pattern"),
     (lambda g, p: setattr(p, "flags", 8), "flag"),
     (lambda g, p: (setattr(g, "nx", 2048), setattr(g, "ny", 1024), setattr(g, "nz", 1024)), "2^31"),
