@@ -61,8 +61,8 @@ STEP_BYTES_PER_CELL_16 = COLLIDE_BYTES_PER_CELL_16 + (7 * 2 + 4 + 4) + 8
 # the kernel source it was taken on (hash of csrc/lbm_device.cuh, lbm_cells.cuh and
 # lbm_kernels.cu).
 NCU_TRAFFIC = {
-    # profiles/step_kernels_rt128x128x512_full.md: 1704.7 MB per launch over 8,388,608
-    # cells (ncu --set full on the 128x128x512 case, scaled by cells to the benchmark)
+    # 1704.7 MB per launch over 8,388,608 cells (ncu --set full on the 128x128x512
+    # case, scaled by cells to the benchmark)
     "k_collide": {"bytes_per_cell": 203.22, "kernel_sha": "f0da994cbf15259d"},
 }
 

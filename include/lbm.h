@@ -227,10 +227,13 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * (coupled model, after the first step, while not profiling), 0 launches every kernel;
  * identical results.  LBM_TUNE_TMA_WAIT_POLLS: how many times a block of the TMA
  * chemical-potential pass polls for its copy before giving up (default 2^22, far more
- * than a copy takes); a block that gives up sets the error word that the next
- * lbm_reduce, lbm_step_reduce or lbm_read_fields reports as LBM_ETIMEOUT, and that
- * step's results are not valid.  0 makes every wait give up at once, which exercises
- * the failure path.
+ * than a copy takes); a block that gives up waits once more (2^22 polls) for its copy
+ * to land and returns, setting the error word that the next lbm_reduce,
+ * lbm_step_reduce or lbm_read_fields reports as LBM_ETIMEOUT, and that step's results
+ * are not valid.  If the copy had not landed even then, the call reports LBM_ECUDA
+ * instead and retires the context: every later call that launches work on it fails
+ * with LBM_ECUDA, and it can only be destroyed.  0 makes every first wait give up at
+ * once, which exercises the recoverable path.
  * LBM_TUNE_ROWS: 1 (default) lets the order-parameter and stream-collide passes address
  * the populations they exchange with neighbouring cells a whole row of tiles at a time
  * (the pulls of LBM_PATTERN_AB, the reads and writes of the odd LBM_PATTERN_AA steps),
@@ -270,8 +273,11 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms,
  * process exits).  n must lie in [0, 2^31 - 1], else LBM_EINVAL with a message in
  * lbm_last_error(NULL).  Asynchronous on `cuda_stream`.  The first call on each device
  * looks up the scratch address on that device; make that first call before any stream
- * capture.  All calls on a device share the scratch, so calls that overlap on the GPU
- * (other streams, other host threads) race and give wrong sums; serialise them. */
+ * capture.  The address is kept for the life of the process, so do not call this
+ * function again after cudaDeviceReset (or any other teardown of the device's primary
+ * context) in the same process.  All calls on a device share the scratch, so calls that
+ * overlap on the GPU (other streams, other host threads) race and give wrong sums;
+ * serialise them. */
 lbm_status lbm_field_sum_noalloc(const float* field, long long n, double* out,
                                  void* cuda_stream);
 

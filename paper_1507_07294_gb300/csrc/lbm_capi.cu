@@ -61,6 +61,7 @@ struct lbm_ctx {
   bool odd = false;        // parity of the stored populations (pattern AA)
   bool have_prev = false;  // phiu holds the previous step's phi u
   bool initialized = false;
+  bool retired = false;    // a TMA copy may have outlived its block: no more launches
 
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events[3];
@@ -206,15 +207,33 @@ void release(lbm_ctx* c) {
 // Device error word (1: a bounded wait on a TMA copy ran out), kept in red[7].
 int* error_word(lbm_ctx* c) { return reinterpret_cast<int*>(c->red + 7); }
 
-// Reports and clears the error word, given a host copy of red[0..7].
+// Reports and clears the error word, given a host copy of red[0..7].  Word 1: a bounded
+// wait for a TMA copy ran out, the copy then landed and the block returned; the steps
+// since are invalid but the context is usable.  Word 2: the copy had not landed when
+// its block returned, so it may have written into shared memory the block no longer
+// owned; the context is retired (every later launching call fails).
 lbm_status take_device_error(lbm_ctx* c, const double* h) {
   int word = 0;
   std::memcpy(&word, h + 7, sizeof(word));
   if (word == 0) return LBM_OK;
   cudaMemsetAsync(c->red + 7, 0, sizeof(double), c->stream);
+  if (word >= 2) {
+    c->retired = true;
+    return fail(c, LBM_ECUDA,
+                "a TMA copy in the chemical-potential pass had not landed when its block "
+                "returned; the context is retired (destroy it)");
+  }
   return fail(c, LBM_ETIMEOUT,
               "a bounded wait for a TMA copy in the chemical-potential pass ran out; the "
               "affected steps are not valid");
+}
+
+// Refuses launches on a context that is not initialised or has been retired.
+lbm_status check_ready(lbm_ctx* c, bool need_init = true) {
+  if (c->retired) return fail(c, LBM_ECUDA, "context retired after a TMA copy outlived its block");
+  if (need_init && !c->initialized)
+    return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  return LBM_OK;
 }
 
 // The chemical-potential pass can fetch its halo bricks by TMA when whole bricks tile
@@ -303,6 +322,8 @@ bool lbm::ctx_batchable(const lbm_ctx* c, std::string* why) {
   const char* r = nullptr;
   if (!c->initialized)
     r = "not initialised";
+  else if (c->retired)
+    r = "retired after a TMA copy outlived its block";
   else if (c->params.pattern != LBM_PATTERN_AB)
     r = "batches need LBM_PATTERN_AB";
   else if (c->vel_kind != LBM_VELOCITY_NONE)
@@ -513,6 +534,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
 
 lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const double* p) {
   if (!c) return LBM_EINVAL;
+  if (const lbm_status rs = check_ready(c, false); rs != LBM_OK) return rs;
   if (!phi) return fail(c, LBM_EINVAL, "phi must not be NULL");
   const size_t n = static_cast<size_t>(c->geo.n);
   const size_t s = c->geo.stride;
@@ -548,7 +570,7 @@ lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const do
 lbm_status lbm_step(lbm_ctx* c, int n) {
   if (!c) return LBM_EINVAL;
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
-  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
   int it = 0;
   if (n >= 2 && c->use_graphs && c->vel_kind == LBM_VELOCITY_NONE && !c->profiling &&
       !c->have_prev) {
@@ -579,7 +601,7 @@ lbm_status lbm_step_reduce_async(lbm_ctx* c, int n, double* out_dev) {
   if (n < 1) return fail(c, LBM_EINVAL, "n must be >= 1");
   if (!out_dev || reinterpret_cast<uintptr_t>(out_dev) % alignof(double) != 0)
     return fail(c, LBM_EINVAL, "out_dev must be a non-NULL, 8-byte aligned pointer");
-  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
   if (!fused_sums(c)) {
     const lbm_status st = lbm_step(c, n);
     return st != LBM_OK ? st : lbm_reduce_async(c, out_dev);
@@ -609,7 +631,7 @@ lbm_status lbm_step_reduce(lbm_ctx* c, int n, double* sum_phi, double mom[3]) {
 lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, double* p,
                            double* u, double* mu) {
   if (!c) return LBM_EINVAL;
-  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
   if (((mask & LBM_FIELD_PHI) && !phi) || ((mask & LBM_FIELD_RHO) && !rho) ||
       ((mask & LBM_FIELD_P) && !p) || ((mask & LBM_FIELD_U) && !u) || ((mask & LBM_FIELD_MU) && !mu))
     return fail(c, LBM_EINVAL, "a selected field has a NULL buffer");
@@ -646,7 +668,7 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
 lbm_status lbm_reduce(lbm_ctx* c, double* sum_phi, double mom[3]) {
   if (!c) return LBM_EINVAL;
   if (!sum_phi || !mom) return fail(c, LBM_EINVAL, "outputs must not be NULL");
-  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
   float* phi_now = c->stage + 5 * c->geo.stride;
   LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, phi_now, c->geo, read_pattern(c), c->stream));
   LBM_CK(c, lbm::launch_reduce(cur_state(c), phi_now, c->partial, c->red, c->geo, read_pattern(c),
@@ -668,7 +690,7 @@ lbm_status lbm_reduce_async(lbm_ctx* c, double* out_dev) {
   if (!c) return LBM_EINVAL;
   if (!out_dev || reinterpret_cast<uintptr_t>(out_dev) % alignof(double) != 0)
     return fail(c, LBM_EINVAL, "out_dev must be a non-NULL, 8-byte aligned pointer");
-  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
   float* phi_now = c->stage + 5 * c->geo.stride;
   LBM_CK(c, lbm::launch_phi(cur_state(c), c->phi, phi_now, c->geo, read_pattern(c), c->stream));
   LBM_CK(c, lbm::launch_reduce(cur_state(c), phi_now, c->partial, out_dev, c->geo,
@@ -678,7 +700,7 @@ lbm_status lbm_reduce_async(lbm_ctx* c, double* out_dev) {
 
 lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long long* step) {
   if (!c) return LBM_EINVAL;
-  if (!c->initialized) return fail(c, LBM_EINVAL, "lbm_init_phi or lbm_write_state first");
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
   const size_t n = static_cast<size_t>(c->geo.n);
   for (int q = 0; q < lbm::kTileSlots; ++q) {
     float* dst = nullptr;
@@ -702,6 +724,7 @@ lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long
 lbm_status lbm_write_state(lbm_ctx* c, const float* f, const float* g, const float* phiu_prev,
                            long long step) {
   if (!c) return LBM_EINVAL;
+  if (const lbm_status rs = check_ready(c, false); rs != LBM_OK) return rs;
   if (!f || !g) return fail(c, LBM_EINVAL, "f and g must not be NULL");
   if (step < 0) return fail(c, LBM_EINVAL, "step must be >= 0");
   const size_t n = static_cast<size_t>(c->geo.n);

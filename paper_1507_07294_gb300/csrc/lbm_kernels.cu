@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
 // the grid arrive as zeros and are then replaced, on boundary bricks only, by their
 // periodic image or wall ghost with plain loads.  Needs nx % 32 == 0 and ny % 8 == 0
 // (whole bricks in x and y).  The wait on the copy's mbarrier is bounded: if it runs
-// out (after `polls` polls; kMbarSpins by default), the block sets *err, waits once
-// more (bounded) for its copy, and returns.
+// out (after `polls` polls; kMbarSpins by default), the block waits once more (bounded,
+// kMbarSpins polls) for its copy and returns, setting *err to at least 1 if the copy
+// landed in that second wait and to 2 if it did not.
 constexpr int kBX = kTX + 8;  // 4 columns either side; the stencil uses columns 3 .. 36
 constexpr unsigned kMuBoxBytes = kBX * kHY * kHZ * 4;
 constexpr long long kMbarSpins = 1 << 22;
@@ -210,8 +211,10 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
   }
   if (!__syncthreads_and(mbar_wait(bar, 0, polls))) {
     if (tid == 0) {
-      atomicExch(err, 1);
-      mbar_wait(bar, 0, kMbarSpins);  // let the copy into this block's shared memory land
+      // let the copy into this block's shared memory land; if even that bounded wait
+      // runs out, the copy may still be writing when the block exits: word 2 tells the
+      // host to retire the context (no further launches on it)
+      atomicMax(err, mbar_wait(bar, 0, kMbarSpins) ? 1 : 2);
     }
     __syncthreads();
     return;
@@ -511,7 +514,11 @@ __global__ void __launch_bounds__(kBlock) k_reduce_partial(const float* __restri
                                                            double* __restrict__ partial,
                                                            Geometry geo, int with_g) {
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int idx = blockIdx.x * kBlock + threadIdx.x; idx < geo.n; idx += gridDim.x * kBlock) {
+  // 64-bit loop index: geo.n < 2^31, but the last stride (up to kReduceMaxParts blocks)
+  // could pass INT_MAX; idx itself is < geo.n inside the loop.
+  const long long stride = static_cast<long long>(gridDim.x) * kBlock;
+  for (long long i = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x; i < geo.n; i += stride) {
+    const int idx = static_cast<int>(i);
     float jx = 0.0f, jy = 0.0f, jz = 0.0f;
     if (with_g) {
       int x, y, z;

@@ -52,10 +52,13 @@ cudaError_t scratch_on_current_device(double** out) {
 // Pass 1: block b accumulates elements b*256 + t, striding by the grid, in FP64, then
 // folds its threads in a fixed order into scratch[2b] (sum) and scratch[2b + 1]
 // (non-finite count).  Every pair a call reads is written earlier in the same call.
-__global__ void __launch_bounds__(kThreads) k_sum_partial(const float* __restrict__ x, int n,
+// The index is 64-bit: for n up to 2^31 - 1 the last stride (up to kParts * kThreads =
+// 2^18) would pass INT_MAX, so i stays below n + 2^18 < 2^32 without overflow.
+__global__ void __launch_bounds__(kThreads) k_sum_partial(const float* __restrict__ x, long long n,
                                                           double* __restrict__ scratch) {
   double sum = 0.0, bad = 0.0;
-  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+  const long long stride = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = static_cast<long long>(blockIdx.x) * kThreads + threadIdx.x; i < n; i += stride) {
     const float v = x[i];
     sum += v;
     if (!isfinite(v)) bad += 1.0;
@@ -123,7 +126,7 @@ extern "C" lbm_status lbm_field_sum_noalloc(const float* field, long long n, dou
   const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int blocks = static_cast<int>((n + kThreads - 1) / kThreads);
   const int parts = blocks < 1 ? 1 : (blocks < kParts ? blocks : kParts);
-  k_sum_partial<<<parts, kThreads, 0, st>>>(field, static_cast<int>(n), scratch);
+  k_sum_partial<<<parts, kThreads, 0, st>>>(field, n, scratch);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
     k_sum_final<<<1, kThreads, 0, st>>>(scratch, parts, out);

@@ -99,6 +99,28 @@ def test_hydrostatic_column():
     assert np.abs(fl["u"]).max() < 1e-6
 
 
+@pytest.mark.parametrize("phi_fill", [1.0, -1.0])
+def test_hydrostatic_column_buoyancy_form(phi_fill):
+    """Single fluid between walls under the buoyancy form G = (rho - (rho_l + rho_g)/2) g:
+    the steady state has u = 0 and dp/dz = -(rho - rho_mean) g.  With rho_l = 3,
+    rho_g = 1 the liquid column (phi = 1) feels +1 x g and the gas column (phi = -1)
+    -1 x g, so the pressure gradient has the gas column's sign reversed; the plain
+    weight would give -3 g and -1 g."""
+    w = I.flat_interface(nz=12, nxy=1)
+    w.phi0 = np.full(w.shape, phi_fill)
+    w.buoyancy = True
+    gacc = 1e-4
+    w.g = (0.0, 0.0, -gacc)
+    o = _oracle(w)
+    o.step(3000)
+    fl = o.fields()
+    rho = w.rho_l if phi_fill > 0 else w.rho_g
+    p = fl["p"][:, 0, 0]
+    dpdz = np.diff(p)[2:-2]
+    np.testing.assert_allclose(dpdz, -(rho - 0.5 * (w.rho_l + w.rho_g)) * gacc, rtol=1e-3)
+    assert np.abs(fl["u"]).max() < 1e-6
+
+
 def test_shear_wave_decay_gives_eq33_viscosity():
     """u_x = U sin(2 pi z / N) in one fluid decays like exp(-nu k^2 t) with
     nu = c_s^2 (tau_g - 1/2) (Eq. 33)."""

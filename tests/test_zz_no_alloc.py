@@ -59,3 +59,51 @@ def test_matches_lbm_reduce_on_two_calls_in_a_row():
         assert got[1] == 0.0
         sums.append(got[0])
     assert abs(sums[0] - sums[1]) > 1.0
+
+
+@pytest.mark.gpu
+def test_grid_stride_and_the_largest_admitted_size():
+    """Arrays longer than 1024 blocks x 256 threads, so each block of the fixed grid
+    strides over several elements, down to n = 2^31 - 1, the largest size the entry
+    point admits (an 8.6 GB FP32 array): the 64-bit stride must neither wrap nor skip
+    the last element."""
+    import torch
+
+    lib = L.load_library()
+    stream = torch.cuda.current_stream().cuda_stream
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+
+    def call(x, n):
+        st = lib.lbm_field_sum_noalloc(ctypes.c_void_p(x.data_ptr()), n,
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+        assert st == L.LBM_OK, lib.lbm_last_error(None).decode()
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    for n in (1024 * 256 + 1, 3 * 1024 * 256 + 77, 40_000_003):
+        x = torch.rand(n, generator=gen, device="cuda", dtype=torch.float32) - 0.25
+        x[n // 3] = float("inf")
+        got = call(x, n - 1)  # the last element is outside the summed range
+        assert got[1] == 1.0
+        x[n // 3] = 0.0
+        ref = float(x[: n - 1].double().sum())
+        got = call(x, n - 1)
+        assert got[1] == 0.0
+        assert abs(got[0] - ref) <= 1e-12 * float(x.abs().double().sum())
+        del x
+
+    n = 2 ** 31 - 1
+    free, _ = torch.cuda.mem_get_info()
+    if free < 4 * n + (2 << 30):
+        pytest.skip("not enough free device memory for a 2^31 - 1 element array")
+    x = torch.full((n,), 0.25, dtype=torch.float32, device="cuda")
+    x[-1] = 1.0
+    got = call(x, n)
+    # every partial sum is a multiple of 1/4 below 2^30: exact in FP64
+    assert got[0] == (n - 1) * 0.25 + 1.0
+    assert got[1] == 0.0
+    x[-1] = float("nan")
+    assert call(x, n)[1] == 1.0
+    del x
+    torch.cuda.empty_cache()
