@@ -239,6 +239,17 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * (the pulls of LBM_PATTERN_AB, the reads and writes of the odd LBM_PATTERN_AA steps),
  * which needs nx a multiple of 32 (lbm_get_tuning reports 1 only while it is in use);
  * 0 keeps the per-cell addressing everywhere.  Identical results.
+ * LBM_TUNE_FUSED: 1 runs each step as ONE kernel instead of three (default 0) where it
+ * applies -- LBM_PATTERN_AB, the coupled model without LBM_FLAG_SRT_FLOW or
+ * LBM_FLAG_D3Q7_STENCIL, nx a multiple of 32 and ny a multiple of 8: every block
+ * marches up z through a 32 x 8 column of cells, forming phi (with a 2-cell halo) and
+ * mu (1-cell halo) in shared memory a plane or two ahead of the collision, so neither
+ * goes through global memory and the 7 f slots are read once (200 B per cell instead
+ * of 248 in FP32).  lbm_get_tuning reports 1 only while it applies.  Identical results
+ * to the three-kernel step.  LBM_TUNE_FUSED_SEGMENT: planes of z per block (0, the
+ * default, chooses by grid size; each segment also forms phi on 2 planes and mu on 1
+ * plane beyond each of its ends).  LBM_TUNE_FUSED_PREFETCH: how many planes ahead each
+ * block prefetches its tiles into L2 (default 2, 0 off, at most 64).
  * Setting any parameter drops the captured graphs (and waits for the context's
  * stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */
@@ -248,6 +259,9 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
 #define LBM_TUNE_GRAPHS 3
 #define LBM_TUNE_TMA_WAIT_POLLS 4
 #define LBM_TUNE_ROWS 5
+#define LBM_TUNE_FUSED 6
+#define LBM_TUNE_FUSED_SEGMENT 7
+#define LBM_TUNE_FUSED_PREFETCH 8
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 
@@ -257,8 +271,8 @@ lbm_status lbm_get_step(const lbm_ctx* ctx, long long* step);
 /* Per-kernel timing with CUDA events on the context's stream.  While enabled,
  * lbm_step brackets each kernel launch with events.  lbm_profile_read synchronises,
  * then returns for kernel k (0: order parameter, 1: chemical potential, 2: fused
- * stream-collide) the summed duration in ms and the number of launches since the
- * last lbm_profile(ctx, 1). */
+ * stream-collide, or the single-pass step kernel where LBM_TUNE_FUSED applies) the
+ * summed duration in ms and the number of launches since the last lbm_profile(ctx, 1). */
 lbm_status lbm_profile(lbm_ctx* ctx, int enable);
 lbm_status lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms,
                             long long* launches);

@@ -31,7 +31,12 @@ struct lbm_ctx {
   // device memory
   float* pop[2] = {nullptr, nullptr};  // tiled cell state(s): 22 populations + phi u
   int cur = 0;             // array holding the current state (pattern AB)
-  float* phi = nullptr;    // order parameter of the current step
+  float* phi = nullptr;    // order parameter of the current step: phi_buf[phi_sel]
+  // phi_buf[1] exists only with 16-bit storage on grids the single-pass step takes: that
+  // step reads the previous step's phi (the shift of slot 0) from one array while it
+  // writes the new phi into the other
+  float* phi_buf[2] = {nullptr, nullptr};
+  int phi_sel = 0;
   float* mu = nullptr;     // chemical potential of the current step
   float* stage = nullptr;  // 7 planes: field read-out (rho, p, u, phi, mu), state
                            // gather/scatter, initial u and p
@@ -39,17 +44,26 @@ struct lbm_ctx {
   double* red = nullptr;      // 5 reduction results; red[7] holds the device error word
   double* step_parts = nullptr;  // per-warp partials of the fused step sums
 
-  // TMA descriptor of phi for the chemical-potential pass (when the grid allows it)
-  CUtensorMap phi_map{};
+  // TMA descriptors of phi_buf[0], phi_buf[1] for the chemical-potential pass (when the
+  // grid allows it)
+  CUtensorMap phi_map[2]{};
   bool have_phi_map = false;
   bool use_phi_map = true;
   long long tma_polls = -1;  // poll budget of the copy's wait; -1: the kernel default
   int row_tiles = 0;         // Geometry::row_tiles when LBM_TUNE_ROWS is on
 
+  // single-pass step (lbm_fused.cu): enabled, planes per segment (0: by grid size), L2
+  // prefetch distance in planes
+  bool use_fused = false;
+  int fused_seg = 0;
+  int fused_pf = 2;
+  int sms = 0;
+
   // CUDA graphs of two consecutive steps, one per parity of the stored state (which
-  // array is current, or the AA step parity), replayed by lbm_step; captured on first
-  // use, dropped whenever a kernel argument changes (tuning, prescribed velocity)
-  cudaGraphExec_t pair_graph[2] = {nullptr, nullptr};
+  // array is current, or the AA step parity, and which phi array is current), replayed
+  // by lbm_step; captured on first use, dropped whenever a kernel argument changes
+  // (tuning, prescribed velocity)
+  cudaGraphExec_t pair_graph[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
   bool use_graphs = true;
 
@@ -194,13 +208,14 @@ void release(lbm_ctx* c) {
     }
   dev_free(c, c->pop[0]);
   dev_free(c, c->pop[1]);
-  dev_free(c, c->phi);
+  dev_free(c, c->phi_buf[0]);
+  dev_free(c, c->phi_buf[1]);
   dev_free(c, c->mu);
   dev_free(c, c->stage);
   dev_free(c, c->partial);
   dev_free(c, c->red);
   dev_free(c, c->step_parts);
-  c->pop[0] = c->pop[1] = c->phi = c->mu = c->stage = nullptr;
+  c->pop[0] = c->pop[1] = c->phi = c->phi_buf[0] = c->phi_buf[1] = c->mu = c->stage = nullptr;
   c->partial = c->red = c->step_parts = nullptr;
 }
 
@@ -238,11 +253,12 @@ lbm_status check_ready(lbm_ctx* c, bool need_init = true) {
 
 // The chemical-potential pass can fetch its halo bricks by TMA when whole bricks tile
 // x and y, the box fits the grid, and phi starts on a 16-byte boundary.
-bool encode_phi_map(lbm_ctx* c) {
+bool encode_phi_map(lbm_ctx* c, int which) {
   const lbm::Geometry& g = c->geo;
+  float* phi = c->phi_buf[which];
   if (!lbm::mu_tma_shape_ok(g) || g.nx < static_cast<int>(lbm::kMuTmaBox[0]) ||
       g.ny < static_cast<int>(lbm::kMuTmaBox[1]) || g.nz < static_cast<int>(lbm::kMuTmaBox[2]) ||
-      reinterpret_cast<uintptr_t>(c->phi) % 16 != 0)
+      reinterpret_cast<uintptr_t>(phi) % 16 != 0)
     return false;
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -261,7 +277,7 @@ bool encode_phi_map(lbm_ctx* c) {
                                  static_cast<cuuint64_t>(g.nx) * g.ny * 4};
   const cuuint32_t box[3] = {lbm::kMuTmaBox[0], lbm::kMuTmaBox[1], lbm::kMuTmaBox[2]};
   const cuuint32_t elem[3] = {1, 1, 1};
-  return encode(&c->phi_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->phi, dims, strides, box, elem,
+  return encode(&c->phi_map[which], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, phi, dims, strides, box, elem,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
@@ -270,6 +286,27 @@ bool encode_phi_map(lbm_ctx* c) {
 // Per-warp partials of the fused step sums: 5 doubles per 32 cells.
 size_t step_parts_bytes(long long n) {
   return static_cast<size_t>(lbm::cell_warps(n)) * 5 * sizeof(double);
+}
+
+// Whether a context of this grid and these parameters keeps a second phi array (16-bit
+// storage on grids the single-pass step takes).
+bool wants_phi_alt(const lbm_grid& g, const lbm_params& p) {
+  return p.storage != LBM_STORAGE_FP32 && p.pattern == LBM_PATTERN_AB && g.nx % lbm::kTile == 0 &&
+         g.ny % 8 == 0 &&
+         static_cast<long long>(g.ny) * (g.nx / lbm::kTile) * lbm::tile_bytes<lbm::kF32>() <
+             (1LL << 31);
+}
+
+// Whether the next step goes through the single-pass kernel.
+bool fused_applies(const lbm_ctx* c) {
+  return c->use_fused && c->vel_kind == LBM_VELOCITY_NONE && c->params.pattern == LBM_PATTERN_AB &&
+         !(c->params.flags & (LBM_FLAG_SRT_FLOW | LBM_FLAG_D3Q7_STENCIL)) &&
+         lbm::fused_shape_ok(c->geo) && (c->geo.storage == lbm::kF32 || c->phi_buf[1]);
+}
+
+int fused_segment(const lbm_ctx* c) {
+  if (c->fused_seg > 0) return c->fused_seg < c->geo.nz ? c->fused_seg : c->geo.nz;
+  return lbm::fused_default_segment(c->geo, c->sms);
 }
 
 // Pattern of the next step's reads of the current state.
@@ -363,10 +400,27 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
   const int pat = read_pattern(c);
   const float* src = cur_state(c);
   float* dst = c->params.pattern == LBM_PATTERN_AB ? c->pop[1 - c->cur] : c->pop[c->cur];
+  if (fused_applies(c)) {
+    float* phi_out = c->geo.storage != lbm::kF32 ? c->phi_buf[1 - c->phi_sel] : nullptr;
+    LBM_CK(c, timed(c, 2, [&] {
+             return lbm::launch_fused(src, dst, c->phi, phi_out, c->geo, c->ph, c->have_prev,
+                                      fused_segment(c), c->fused_pf,
+                                      sums_out ? c->step_parts : nullptr, c->partial, sums_out,
+                                      c->stream);
+           }));
+    if (phi_out) {
+      c->phi_sel = 1 - c->phi_sel;
+      c->phi = c->phi_buf[c->phi_sel];
+    }
+    c->cur = 1 - c->cur;
+    c->have_prev = true;
+    ++c->step;
+    return LBM_OK;
+  }
   LBM_CK(c, timed(c, 0, [&] { return lbm::launch_phi(src, c->phi, c->phi, c->geo, pat, c->stream); }));
   LBM_CK(c, timed(c, 1, [&] {
            return c->have_phi_map && c->use_phi_map
-                      ? lbm::launch_mu_tma(c->phi_map, c->phi, c->mu, c->geo, c->ph,
+                      ? lbm::launch_mu_tma(c->phi_map[c->phi_sel], c->phi, c->mu, c->geo, c->ph,
                                            error_word(c),
                                            c->tma_polls < 0 ? lbm::mu_tma_default_polls()
                                                             : c->tma_polls,
@@ -405,7 +459,7 @@ bool graphs_apply(const lbm_ctx* c) {
 }
 
 int pair_parity(const lbm_ctx* c) {
-  return c->params.pattern == LBM_PATTERN_AB ? c->cur : (c->odd ? 1 : 0);
+  return (c->params.pattern == LBM_PATTERN_AB ? c->cur : (c->odd ? 1 : 0)) | (c->phi_sel << 1);
 }
 
 // Captures two steps from the current parity into c->pair_graph[parity]; the context's
@@ -414,7 +468,7 @@ lbm_status capture_pair(lbm_ctx* c, int parity) {
   if (!c->capture_stream &&
       cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(c, LBM_ECUDA, "cudaStreamCreate failed (graph capture)");
-  const int cur = c->cur;
+  const int cur = c->cur, phi_sel = c->phi_sel;
   const bool odd = c->odd, have_prev = c->have_prev;
   const long long step = c->step;
   cudaStream_t stream = c->stream;
@@ -429,6 +483,8 @@ lbm_status capture_pair(lbm_ctx* c, int parity) {
   const cudaError_t ec = e == cudaSuccess ? cudaStreamEndCapture(c->capture_stream, &graph) : e;
   c->stream = stream;
   c->cur = cur;
+  c->phi_sel = phi_sel;
+  c->phi = c->phi_buf[phi_sel];
   c->odd = odd;
   c->have_prev = have_prev;
   c->step = step;
@@ -501,18 +557,27 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     }
   }
   c->ph = make_physics(*params);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      c->sms = 0;
+  }
 
   const size_t plane = c->geo.stride * sizeof(float);
   const size_t state_bytes = lbm::state_bytes(c->geo.n, c->geo.storage);
   c->pop[0] = static_cast<float*>(dev_alloc(c, state_bytes));
   if (params->pattern == LBM_PATTERN_AB) c->pop[1] = static_cast<float*>(dev_alloc(c, state_bytes));
-  c->phi = static_cast<float*>(dev_alloc(c, plane));
+  c->phi = c->phi_buf[0] = static_cast<float*>(dev_alloc(c, plane));
+  const bool need_alt = wants_phi_alt(*grid, *params);
+  if (need_alt) c->phi_buf[1] = static_cast<float*>(dev_alloc(c, plane));
   c->mu = static_cast<float*>(dev_alloc(c, plane));
   c->stage = static_cast<float*>(dev_alloc(c, plane * 7));
   c->partial = static_cast<double*>(dev_alloc(c, sizeof(double) * 5 * lbm::kReduceMaxParts));
   c->red = static_cast<double*>(dev_alloc(c, sizeof(double) * 8));
   c->step_parts = static_cast<double*>(dev_alloc(c, step_parts_bytes(c->geo.n)));
-  if (!c->pop[0] || (params->pattern == LBM_PATTERN_AB && !c->pop[1]) || !c->phi || !c->mu ||
+  if (!c->pop[0] || (params->pattern == LBM_PATTERN_AB && !c->pop[1]) || !c->phi ||
+      (need_alt && !c->phi_buf[1]) || !c->mu ||
       !c->stage || !c->partial || !c->red || !c->step_parts) {
     release(c);
     delete c;
@@ -521,7 +586,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   cudaError_t e = cudaMemsetAsync(c->pop[0], 0, state_bytes, c->stream);
   if (e == cudaSuccess && c->pop[1]) e = cudaMemsetAsync(c->pop[1], 0, state_bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->red, 0, sizeof(double) * 8, c->stream);
-  c->have_phi_map = encode_phi_map(c);
+  c->have_phi_map = encode_phi_map(c, 0) && (!c->phi_buf[1] || encode_phi_map(c, 1));
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     release(c);
@@ -792,6 +857,18 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_ROWS takes 0 or 1");
       c->geo.row_tiles = value == 1 ? c->row_tiles : 0;
       break;
+    case LBM_TUNE_FUSED:
+      if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_FUSED takes 0 or 1");
+      c->use_fused = value == 1;
+      break;
+    case LBM_TUNE_FUSED_SEGMENT:
+      if (value > (1 << 20)) return fail(c, LBM_EINVAL, "LBM_TUNE_FUSED_SEGMENT out of range");
+      c->fused_seg = value;
+      break;
+    case LBM_TUNE_FUSED_PREFETCH:
+      if (value > 64) return fail(c, LBM_EINVAL, "LBM_TUNE_FUSED_PREFETCH takes 0..64");
+      c->fused_pf = value;
+      break;
     default: return fail(c, LBM_EINVAL, "unknown tuning parameter");
   }
   cudaStreamSynchronize(c->stream);  // a replay may still be running
@@ -812,6 +889,9 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
     case LBM_TUNE_ROWS:
       *value = c->geo.row_tiles > 0 ? 1 : 0;
       return LBM_OK;
+    case LBM_TUNE_FUSED: *value = fused_applies(c) ? 1 : 0; return LBM_OK;
+    case LBM_TUNE_FUSED_SEGMENT: *value = fused_segment(c); return LBM_OK;
+    case LBM_TUNE_FUSED_PREFETCH: *value = c->fused_pf; return LBM_OK;
     default: return LBM_EINVAL;
   }
 }
@@ -858,7 +938,8 @@ lbm_status lbm_memory_bytes(const lbm_grid* grid, const lbm_params* params, size
   const long long n = static_cast<long long>(grid->nx) * grid->ny * grid->nz;
   const size_t plane = static_cast<size_t>((n + 63) / 64 * 64) * sizeof(float);
   const size_t state = lbm::state_bytes(static_cast<int>(n), params->storage);
-  *bytes = state * (params->pattern == LBM_PATTERN_AB ? 2 : 1) + plane * 9 +
+  *bytes = state * (params->pattern == LBM_PATTERN_AB ? 2 : 1) +
+           plane * (wants_phi_alt(*grid, *params) ? 10 : 9) +
            sizeof(double) * (5 * lbm::kReduceMaxParts + 8) + step_parts_bytes(n);
   return LBM_OK;
 }

@@ -299,29 +299,33 @@ __device__ __forceinline__ CellStencils cell_stencils(const float* __restrict__ 
 // velocity, so sum phi = sum of all post-collision f, and the lattice momentum = sum of
 // c_i g_i with c_i negated for the populations that bounce.  Each value is taken as the
 // next step will read it back from storage (16-bit rounding, the slot-0 shift undone).
-template <int P, int VAR, int S, bool SUMS = false>
-__device__ __forceinline__ void collide_cell(const float* src, float* dst,
-                                             const float* __restrict__ phi,
-                                             const float* __restrict__ mu, const Geometry& geo,
-                                             const Physics& ph, int have_prev, int idx,
-                                             float* sums = nullptr) {
-  int x, y, z;
-  cell_coords(geo, idx, x, y, z);
-  const Nbr nb = make_nbr(geo, x, y, z);
-
-  float g[15], f[7], prev[3];
+// The cell-state reads of the stream-collide body: the pulled g (and, with LOAD_F, f) of
+// pattern P and phi u of the previous step.
+template <int P, int S, bool LOAD_F>
+__device__ __forceinline__ void load_cell(const float* src, const Geometry& geo, int idx,
+                                          const Nbr& nb, float g[15], float f[7], float prev[3]) {
   if (use_rows<P>(geo, nb)) {
     const RowPull r = row_pull<S>(src, nb, idx);
     row_load_g<P, S>(r, g);
-    row_load_f<P, S>(r, f);
+    if (LOAD_F) row_load_f<P, S>(r, f);
   } else {
     load_g<P, S>(src, idx, nb, g);
-    load_f<P, S>(src, idx, nb, f);
+    if (LOAD_F) load_f<P, S>(src, idx, nb, f);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) prev[a] = src[phiu_index<S>(idx, a)];
+}
 
-  const CellStencils cs = cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb);
+// collide_loaded is the body for a cell whose populations are loaded; `stencils()`
+// returns its CellStencils (from the global phi and mu arrays in collide_cell, from
+// shared-memory planes in the fused single-pass kernel).  The values it is given are
+// the only inputs that differ between the two, so both give the same bits.
+template <int P, int VAR, int S, bool SUMS, typename StencilFn>
+__device__ __forceinline__ void collide_loaded(float* dst, const Geometry& geo, const Physics& ph,
+                                               int have_prev, int idx, const Nbr& nb,
+                                               float g[15], float f[7], const float prev[3],
+                                               StencilFn stencils, float* sums) {
+  const CellStencils cs = stencils();
   const Moments15 mo = moments15(g);
   const Macro M = macroscopic(ph, mo, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
   const float lambda_visc = __fdividef(1.0f, 3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
@@ -378,6 +382,53 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
     row_store_f_odd<S>(row_pull<S>(dst, nb, idx), f);
   else
     store_f<P, S>(dst, idx, nb, f);
+}
+
+template <int P, int VAR, int S, bool SUMS, typename StencilFn>
+__device__ __forceinline__ void collide_cell_at(const float* src, float* dst, const Geometry& geo,
+                                                const Physics& ph, int have_prev, int idx,
+                                                const Nbr& nb, StencilFn stencils, float* sums) {
+  float g[15], f[7], prev[3];
+  load_cell<P, S, true>(src, geo, idx, nb, g, f, prev);
+  collide_loaded<P, VAR, S, SUMS>(dst, geo, ph, have_prev, idx, nb, g, f, prev, stencils, sums);
+}
+
+template <int P, int VAR, int S, bool SUMS = false>
+__device__ __forceinline__ void collide_cell(const float* src, float* dst,
+                                             const float* __restrict__ phi,
+                                             const float* __restrict__ mu, const Geometry& geo,
+                                             const Physics& ph, int have_prev, int idx,
+                                             float* sums = nullptr) {
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const Nbr nb = make_nbr(geo, x, y, z);
+  collide_cell_at<P, VAR, S, SUMS>(
+      src, dst, geo, ph, have_prev, idx, nb,
+      [&] { return cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb); }, sums);
+}
+
+// Sums of the fused step sums over the 32 cells of a warp, stored as 5 doubles at
+// parts[5 w] (w = the warp's first cell / 32): sum phi, momentum x, y, z and the count
+// of cells with a non-finite contribution.  The four sums take 6 shuffles instead of
+// 20: across lane bit 4 a lane keeps two values and hands its partner the other two,
+// across bit 3 one of those, so that lane l then carries value 2 (l >> 4 & 1) +
+// (l >> 3 & 1) over 4 lanes; three butterfly levels over bits 2..0 complete each sum in
+// its group of 8 lanes.  All 32 lanes must call it.
+__device__ __forceinline__ void warp_sums_store(const float s[4], bool bad, double* parts,
+                                                long long first_cell) {
+  const unsigned nbad = __popc(__ballot_sync(0xffffffffu, bad));
+  const unsigned lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8;
+  const float keep0 = b4 ? s[2] : s[0], keep1 = b4 ? s[3] : s[1];
+  const float give0 = b4 ? s[0] : s[2], give1 = b4 ? s[1] : s[3];
+  const float a0 = keep0 + __shfl_xor_sync(0xffffffffu, give0, 16);
+  const float a1 = keep1 + __shfl_xor_sync(0xffffffffu, give1, 16);
+  float v = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  double* out = parts + static_cast<size_t>(first_cell >> 5) * 5;
+  if ((lane & 7) == 0) out[lane >> 3] = static_cast<double>(v);
+  if (lane == 0) out[4] = static_cast<double>(nbad);
 }
 
 }  // namespace lbm

@@ -664,42 +664,61 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
 // ---------------------------------------------------------------------------------
 // With SHIFT0 (16-bit storage) f[0] is not read: f_0 = phi - sum_{i>0} f_i, so
 // m_0 = phi and m_4 = 6 phi - 7 sum_{i>0} f_i; on return f[0] holds f_0^+ - phi.
+// Every scalar product and sum here is written with an explicit rounding intrinsic
+// (__fmul_rn, __fadd_rn, __fsub_rn, __fmaf_rn), which the compiler never contracts or
+// splits, so the result is the same bits in every kernel that inlines it (left to
+// itself, the compiler fused different multiply-add pairs in different kernels).
 template <bool SHIFT0 = false>
 __device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], float phi, float mu,
                                              const float u[3], const float dphiu[3]) {
   // x and y opposite pairs as paired butterflies, (1, 3) with (2, 4)
   const float2 fp = pr(f[1], f[3]), fm = pr(f[2], f[4]);
   const float2 s_xy = padd(fp, fm), d_xy = psub(fp, fm);
-  const float sz = f[5] + f[6];
-  const float smov = s_xy.x + s_xy.y + sz;
+  const float sz = __fadd_rn(f[5], f[6]);
+  const float smov = __fadd_rn(__fadd_rn(s_xy.x, s_xy.y), sz);
   float m[7];
-  m[0] = SHIFT0 ? phi : f[0] + smov;
+  m[0] = SHIFT0 ? phi : __fadd_rn(f[0], smov);
   m[1] = d_xy.x;
   m[2] = d_xy.y;
-  m[3] = f[5] - f[6];
-  m[4] = SHIFT0 ? 6.0f * phi - 7.0f * smov : 6.0f * f[0] - smov;
-  m[5] = 2.0f * s_xy.x - s_xy.y - sz;
-  m[6] = s_xy.y - sz;
-  const float meq[7] = {phi, phi * u[0], phi * u[1], phi * u[2],
-                        6.0f * phi - 21.0f * ph.A * ph.eta * mu, 0.0f, 0.0f};
-  const float mR[7] = {0.0f, dphiu[0], dphiu[1], dphiu[2], 0.0f, 0.0f, 0.0f};
+  m[3] = __fsub_rn(f[5], f[6]);
+  m[4] = SHIFT0 ? __fmaf_rn(6.0f, phi, __fmul_rn(-7.0f, smov)) : __fmaf_rn(6.0f, f[0], -smov);
+  m[5] = __fsub_rn(__fmaf_rn(2.0f, s_xy.x, -s_xy.y), sz);
+  m[6] = __fsub_rn(s_xy.y, sz);
+  // m - m^eq (Eq. 17); rows 0, 5, 6 have m^eq = phi, 0, 0
+  const float k4 = __fmul_rn(__fmul_rn(21.0f, ph.A), ph.eta);
+  float d[7];
+  d[0] = __fsub_rn(m[0], phi);
+  d[1] = __fsub_rn(m[1], __fmul_rn(phi, u[0]));
+  d[2] = __fsub_rn(m[2], __fmul_rn(phi, u[1]));
+  d[3] = __fsub_rn(m[3], __fmul_rn(phi, u[2]));
+  d[4] = __fsub_rn(m[4], __fmaf_rn(-k4, mu, __fmul_rn(6.0f, phi)));
+  d[5] = m[5];
+  d[6] = m[6];
+  // b_k = [s_k (m_k - m_k^eq) - (1 - s_k/2) mR_k] / |M_k|^2 with mR of Eq. 18
   float b[7];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) b[k] = ph.sf_a[k] * (m[k] - meq[k]) - ph.sf_b[k] * mR[k];
-  const float e = b[0] - b[4];
+  for (int k = 0; k < 7; ++k) {
+    if (k >= 1 && k <= 3)
+      b[k] = __fmaf_rn(ph.sf_a[k], d[k], __fmul_rn(-ph.sf_b[k], dphiu[k - 1]));
+    else
+      b[k] = __fmul_rn(ph.sf_a[k], d[k]);
+  }
+  const float e = __fsub_rn(b[0], b[4]);
+  const float c0 = __fmaf_rn(6.0f, b[4], b[0]);
   if (SHIFT0)
-    f[0] = -(smov + (b[0] + 6.0f * b[4]));
+    f[0] = -__fadd_rn(smov, c0);
   else
-    f[0] -= b[0] + 6.0f * b[4];
-  const float2 e_xy = pr(e + 2.0f * b[5], e - b[5] + b[6]), b12 = pr(b[1], b[2]);
+    f[0] = __fsub_rn(f[0], c0);
+  const float2 e_xy = pr(__fmaf_rn(2.0f, b[5], e), __fadd_rn(__fsub_rn(e, b[5]), b[6]));
+  const float2 b12 = pr(b[1], b[2]);
   const float2 up = psub(fp, padd(e_xy, b12)), dn = psub(fm, psub(e_xy, b12));
   f[1] = up.x;
   f[3] = up.y;
   f[2] = dn.x;
   f[4] = dn.y;
-  const float ez = e - b[5] - b[6];
-  f[5] -= ez + b[3];
-  f[6] -= ez - b[3];
+  const float ez = __fsub_rn(__fsub_rn(e, b[5]), b[6]);
+  f[5] = __fsub_rn(f[5], __fadd_rn(ez, b[3]));
+  f[6] = __fsub_rn(f[6], __fsub_rn(ez, b[3]));
 }
 
 }  // namespace lbm

@@ -71,4 +71,20 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
                                 bool have_prev, double* parts, double* partial, double* out,
                                 cudaStream_t st);
 
+// The fixed-order FP64 reduction of the per-warp partials of the step sums (the tail of
+// launch_collide_sums): parts -> partial -> out (5 doubles).
+cudaError_t launch_step_sums_final(const double* parts, double* partial, double* out,
+                                   const Geometry& geo, cudaStream_t st);
+
+// Single-pass step (lbm_fused.cu): pattern AB, default model variant, grids with
+// fused_shape_ok (nx a multiple of 32 with whole-tile rows, ny a multiple of 8).  phi_in
+// and phi_out (distinct arrays) are read and written with 16-bit storage only.  `seg`
+// planes per block column segment, `pf` L2 prefetch distance in planes (0: none).  With
+// parts non-null the launch also reduces the state it writes, like launch_collide_sums.
+bool fused_shape_ok(const Geometry& geo);
+int fused_default_segment(const Geometry& geo, int sms);
+cudaError_t launch_fused(const float* src, float* dst, const float* phi_in, float* phi_out,
+                         const Geometry& geo, const Physics& ph, bool have_prev, int seg, int pf,
+                         double* parts, double* partial, double* out, cudaStream_t st);
+
 }  // namespace lbm

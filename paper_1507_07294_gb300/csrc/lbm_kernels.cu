@@ -265,11 +265,10 @@ __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
 }
 
 // Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
-// each warp leaves 5 doubles in parts[5 w ..] (w = its first cell / 32): sum phi,
-// momentum x, y, z and the count of cells with a non-finite contribution.  The 32 cells
-// of a warp are summed in FP32 by a fixed butterfly (FP64 throughput on this GPU is a
-// small fraction of FP32, and no block barrier holds finished warps back); everything
-// above in FP64, in a fixed order.
+// each warp leaves 5 doubles in parts[5 w ..] (w = its first cell / 32; warp_sums_store).
+// The 32 cells of a warp are summed in FP32 by a fixed butterfly (FP64 throughput on
+// this GPU is a small fraction of FP32, and no block barrier holds finished warps back);
+// everything above in FP64, in a fixed order.
 template <int P, int S>
 __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
     k_collide_sums(const float* src, float* dst, const float* __restrict__ phi,
@@ -284,23 +283,7 @@ __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
     collide_cell<P, 0, S, true>(src, dst, phi, mu, geo, ph, have_prev, idx, s);
     bad = !(isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3]));
   }
-  const unsigned nbad = __popc(__ballot_sync(0xffffffffu, bad));
-  // Warp sums of the four values with 6 shuffles instead of 20: across lane bit 4 a lane
-  // keeps two values and hands its partner the other two, across bit 3 one of those, so
-  // that lane l then carries value 2 (l >> 4 & 1) + (l >> 3 & 1) over 4 lanes; three
-  // butterfly levels over bits 2..0 complete each sum in its group of 8 lanes.
-  const unsigned lane = threadIdx.x & 31;
-  const bool b4 = lane & 16, b3 = lane & 8;
-  const float keep0 = b4 ? s[2] : s[0], keep1 = b4 ? s[3] : s[1];
-  const float give0 = b4 ? s[0] : s[2], give1 = b4 ? s[1] : s[3];
-  const float a0 = keep0 + __shfl_xor_sync(0xffffffffu, give0, 16);
-  const float a1 = keep1 + __shfl_xor_sync(0xffffffffu, give1, 16);
-  float v = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  double* out = parts + static_cast<size_t>(idx >> 5) * 5;
-  if ((lane & 7) == 0) out[lane >> 3] = static_cast<double>(v);
-  if (lane == 0) out[4] = static_cast<double>(nbad);
+  warp_sums_store(s, bad, parts, idx & ~31);
 }
 
 // ------------------------------------------------------------------ k_che ---------
@@ -715,13 +698,18 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
                                 cudaStream_t st) {
   const int prev = have_prev ? 1 : 0;
   LBM_DISPATCH(geo, pattern, k_collide_sums, src, dst, phi, mu, geo, ph, prev, parts);
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return launch_step_sums_final(parts, partial, out, geo, st);
+}
+
+cudaError_t launch_step_sums_final(const double* parts, double* partial, double* out,
+                                   const Geometry& geo, cudaStream_t st) {
   const int nparts = cell_warps(geo.n);
   const int groups = nparts < kReduceMaxParts ? nparts : kReduceMaxParts;
   const int chunk = (nparts + groups - 1) / groups;
   k_reduce_chunks<<<groups, kBlock, 0, st>>>(parts, nparts, chunk, partial);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_final<<<1, kBlock, 0, st>>>(partial, groups, out);
   return cudaGetLastError();

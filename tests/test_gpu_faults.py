@@ -117,6 +117,7 @@ def test_tma_wait_budget_runs_out_cleanly(L):
     the context keeps working."""
     w = I.perturbed(I.droplet(n=16, R=5.0, nx=64, ny=16, nz=24), seed=51, u_amp=0.01)
     with L.Solver(w) as s:
+        L.lbm_set_tuning(s.ctx, L.LBM_TUNE_FUSED, 0)  # the three-kernel step uses the TMA pass
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_MU_TMA) == 1
         default = L.lbm_get_tuning(s.ctx, L.LBM_TUNE_TMA_WAIT_POLLS)
         assert default > 1000

@@ -338,6 +338,8 @@ def test_tma_halo_path_matches_plain_loads(L, shape, walls):
         w = I.droplet(n=nx, R=min(nx, ny, nz) / 3, nx=nx, ny=ny, nz=nz)
     w = I.perturbed(w, seed=41, u_amp=0.01, p_amp=1e-3)
     with L.Solver(w) as a, L.Solver(w) as b:
+        for s in (a, b):  # the three-kernel step (the single-pass one has no mu pass)
+            L.lbm_set_tuning(s.ctx, L.LBM_TUNE_FUSED, 0)
         assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_MU_TMA) == 1
         L.lbm_set_tuning(b.ctx, L.LBM_TUNE_MU_TMA, 0)
         assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_MU_TMA) == 0
@@ -356,6 +358,7 @@ def test_tma_halo_path_100_steps_against_the_oracle(L):
     w.u0 = np.ascontiguousarray(w.u0[:, :, :16, :])
     w.p0 = np.ascontiguousarray(w.p0[:, :16, :])
     with L.Solver(w) as s:
+        L.lbm_set_tuning(s.ctx, L.LBM_TUNE_FUSED, 0)
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_MU_TMA) == 1
         s.step(100)
         gf = s.fields()
