@@ -250,6 +250,10 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * default, chooses by grid size; each segment also forms phi on 2 planes and mu on 1
  * plane beyond each of its ends).  LBM_TUNE_FUSED_PREFETCH: how many planes ahead each
  * block prefetches its tiles into L2 (default 2, 0 off, at most 64).
+ * LBM_TUNE_CELL_PAIRS: 1 (default) lets the three-kernel step's stream-collide pass of
+ * LBM_PATTERN_AB take two cells per thread (cells x and x + 32 of a row, nx a multiple
+ * of 64), doing the arithmetic of both in paired FP32 instructions; lbm_get_tuning
+ * reports 1 only while it applies.  Identical results.
  * Setting any parameter drops the captured graphs (and waits for the context's
  * stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */
@@ -262,6 +266,7 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
 #define LBM_TUNE_FUSED 6
 #define LBM_TUNE_FUSED_SEGMENT 7
 #define LBM_TUNE_FUSED_PREFETCH 8
+#define LBM_TUNE_CELL_PAIRS 9
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 

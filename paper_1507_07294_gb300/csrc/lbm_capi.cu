@@ -51,6 +51,7 @@ struct lbm_ctx {
   bool use_phi_map = true;
   long long tma_polls = -1;  // poll budget of the copy's wait; -1: the kernel default
   int row_tiles = 0;         // Geometry::row_tiles when LBM_TUNE_ROWS is on
+  int pairs = 0;             // Geometry::pairs when LBM_TUNE_CELL_PAIRS is on
 
   // single-pass step (lbm_fused.cu): enabled, planes per segment (0: by grid size), L2
   // prefetch distance in planes
@@ -545,12 +546,16 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
           (1LL << 31))
     c->row_tiles = grid->nx / lbm::kTile;
   c->geo.row_tiles = c->row_tiles;
+  // two cells per thread in the two-array stream-collide: cells x and x + 32 of one row
+  if (params->pattern == LBM_PATTERN_AB && grid->nx % (2 * lbm::kTile) == 0) c->pairs = 1;
+  c->geo.pairs = c->pairs;
   // L2 prefetch distances: one wave of resident blocks
   {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
-      c->geo.prefetch_collide = sms * lbm::resident_blocks_per_sm(0, c->geo.storage);
+      c->geo.prefetch_collide =
+          sms * lbm::resident_blocks_per_sm(c->geo.pairs ? 3 : 0, c->geo.storage);
       c->geo.prefetch_phi =
           sms * lbm::resident_blocks_per_sm(1, c->geo.storage,
                                             c->geo.row_tiles > 0 && params->pattern == LBM_PATTERN_AB);
@@ -857,6 +862,10 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_ROWS takes 0 or 1");
       c->geo.row_tiles = value == 1 ? c->row_tiles : 0;
       break;
+    case LBM_TUNE_CELL_PAIRS:
+      if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_CELL_PAIRS takes 0 or 1");
+      c->geo.pairs = value == 1 ? c->pairs : 0;
+      break;
     case LBM_TUNE_FUSED:
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_FUSED takes 0 or 1");
       c->use_fused = value == 1;
@@ -889,6 +898,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
     case LBM_TUNE_ROWS:
       *value = c->geo.row_tiles > 0 ? 1 : 0;
       return LBM_OK;
+    case LBM_TUNE_CELL_PAIRS: *value = c->geo.pairs; return LBM_OK;
     case LBM_TUNE_FUSED: *value = fused_applies(c) ? 1 : 0; return LBM_OK;
     case LBM_TUNE_FUSED_SEGMENT: *value = fused_segment(c); return LBM_OK;
     case LBM_TUNE_FUSED_PREFETCH: *value = c->fused_pf; return LBM_OK;

@@ -218,9 +218,7 @@ __device__ __forceinline__ void mu_columns(const float (*tile)[kHY][HX], float* 
     plane(l + 1, c2, f2, d2);
     // Eq. 36 on the D3Q15 stencil: 2/3 (faces - 6 c) + 1/12 (corners - 8 c); with the
     // D3Q7 weights: faces - 6 c
-    const float lap = D3Q7 ? (f1 + (c0 + c2)) - 6.0f * c1
-                           : (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
-                                 (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
+    const float lap = D3Q7 ? lap7_columns(c0, c1, c2, f1) : lap15_columns(c0, c1, c2, f1, d0, d2);
     out[(l - 1) * zstride] = chemical_potential(ph, c1, lap);
     c0 = c1; f0 = f1; d0 = d1;
     c1 = c2; f1 = f2; d1 = d2;
@@ -328,7 +326,7 @@ __device__ __forceinline__ void collide_loaded(float* dst, const Geometry& geo, 
   const CellStencils cs = stencils();
   const Moments15 mo = moments15(g);
   const Macro M = macroscopic(ph, mo, cs.phi, cs.mu, cs.grad_phi, cs.lap_mu);
-  const float lambda_visc = __fdividef(1.0f, 3.0f * (ph.nu_mid + cs.phi * ph.half_dnu) + 0.5f);
+  const float lambda_visc = viscous_rate(ph, cs.phi);
   collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, mo, M, lambda_visc);
   if (SUMS) {
     typedef Elem<S> E;
@@ -364,8 +362,8 @@ __device__ __forceinline__ void collide_loaded(float* dst, const Geometry& geo, 
   float dphiu[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float cur = cs.phi * M.u[a];
-    dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
+    const float cur = __fmul_rn(cs.phi, M.u[a]);
+    dphiu[a] = have_prev ? __fsub_rn(cur, prev[a]) : 0.0f;
     dst[phiu_index<S>(idx, a)] = cur;
   }
 
@@ -405,6 +403,136 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
   collide_cell_at<P, VAR, S, SUMS>(
       src, dst, geo, ph, have_prev, idx, nb,
       [&] { return cell_stencils<(VAR & kVarD3Q7) != 0>(phi, mu, idx, nb); }, sums);
+}
+
+// ------------------------------------------- two cells per thread, paired FP32 -------
+// The stream-collide body for cells idx and idx + kTile (the same lane of two adjacent
+// tiles of one row; pattern AB): loads and stores per cell, every arithmetic step once
+// for both cells in the two lanes of float2 (the generic per-cell math with V = float2),
+// which halves the arithmetic instructions.  Per lane the operations are those of the
+// one-cell body, so each cell gets the same bits.  With SUMS, sums[0..3] and sums[4..7]
+// receive the two cells' contributions (as collide_loaded).
+template <int VAR, int S, bool SUMS>
+__device__ __forceinline__ void collide_pair(const float* src, float* dst,
+                                             const float* __restrict__ phi,
+                                             const float* __restrict__ mu, const Geometry& geo,
+                                             const Physics& ph, int have_prev, int idx,
+                                             float* sums) {
+  typedef VOps<float2> O;
+  constexpr bool D3Q7 = (VAR & kVarD3Q7) != 0;
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const int idx2 = idx + kTile;
+  const Nbr na = make_nbr(geo, x, y, z), nb2 = make_nbr(geo, x + kTile, y, z);
+  float ga[15], fa[7], pa[3], gb[15], fb[7], pb[3];
+  load_cell<kAB, S, true>(src, geo, idx, na, ga, fa, pa);
+  load_cell<kAB, S, true>(src, geo, idx2, nb2, gb, fb, pb);
+  StencilV<float2> sp, sm;
+  {
+    Stencil s0, s1;
+    load_stencil(phi, idx, na, s0);
+    load_stencil(phi, idx2, nb2, s1);
+    sp.c = make_float2(s0.c, s1.c);
+    sp.xm = make_float2(s0.xm, s1.xm);
+    sp.xp = make_float2(s0.xp, s1.xp);
+    sp.ym = make_float2(s0.ym, s1.ym);
+    sp.yp = make_float2(s0.yp, s1.yp);
+    sp.zm = make_float2(s0.zm, s1.zm);
+    sp.zp = make_float2(s0.zp, s1.zp);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sp.k[k] = make_float2(s0.k[k], s1.k[k]);
+  }
+  {
+    Stencil s0, s1;
+    load_stencil(mu, idx, na, s0);
+    load_stencil(mu, idx2, nb2, s1);
+    sm.c = make_float2(s0.c, s1.c);
+    sm.xm = make_float2(s0.xm, s1.xm);
+    sm.xp = make_float2(s0.xp, s1.xp);
+    sm.ym = make_float2(s0.ym, s1.ym);
+    sm.yp = make_float2(s0.yp, s1.yp);
+    sm.zm = make_float2(s0.zm, s1.zm);
+    sm.zp = make_float2(s0.zp, s1.zp);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sm.k[k] = make_float2(s0.k[k], s1.k[k]);
+  }
+  float2 g[15], f[7];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) g[i] = make_float2(ga[i], gb[i]);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i] = make_float2(fa[i], fb[i]);
+  float2 grad_phi[3];
+  if (D3Q7)
+    stencil_grad7(sp, grad_phi);
+  else
+    stencil_grad(sp, grad_phi);
+  const float2 lap_mu = D3Q7 ? stencil_lap7(sm) : stencil_lap(sm);
+  const float2 phc = sp.c, muc = sm.c;
+  const Moments15V<float2> mo = moments15(g);
+  const MacroV<float2> M = macroscopic(ph, mo, phc, muc, grad_phi, lap_mu);
+  const float2 lambda_visc = viscous_rate(ph, phc);
+  collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, mo, M, lambda_visc);
+  typedef Elem<S> E;
+  if (SUMS) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float v[15];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) v[i] = E::get(E::put(c ? g[i].y : g[i].x));
+      const float a7 = v[7] - v[8], a9 = v[9] - v[10], a11 = v[11] - v[12], a13 = v[13] - v[14];
+      float jx = (v[1] - v[2]) + ((a7 + a9) + (a11 + a13));
+      float jy = (v[3] - v[4]) + ((a7 + a9) - (a11 + a13));
+      float jz = (v[5] - v[6]) + ((a7 - a9) + (a11 - a13));
+      if (na.wlo || na.whi) {
+#define X(I, O_, CX, CY, CZ)                                   \
+  if ((CZ > 0 && na.whi) || (CZ < 0 && na.wlo)) {              \
+    jx -= 2.0f * CX * v[I];                                    \
+    jy -= 2.0f * CY * v[I];                                    \
+    jz -= 2.0f * CZ * v[I];                                    \
+  }
+        LBM_D3Q15_LIST(X)
+#undef X
+      }
+      sums[4 * c + 1] = jx;
+      sums[4 * c + 2] = jy;
+      sums[4 * c + 3] = jz;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    ga[i] = g[i].x;
+    gb[i] = g[i].y;
+  }
+  store_g<kAB, S>(dst, idx, na, ga);
+  store_g<kAB, S>(dst, idx2, nb2, gb);
+  // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
+  float2 dphiu[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float2 cur = O::mul(phc, M.u[a]);
+    dphiu[a] = have_prev ? O::sub(cur, make_float2(pa[a], pb[a])) : make_float2(0.0f, 0.0f);
+    dst[phiu_index<S>(idx, a)] = cur.x;
+    dst[phiu_index<S>(idx2, a)] = cur.y;
+  }
+  collide_d3q7<S != kF32>(ph, f, phc, muc, M.u, dphiu);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    fa[i] = f[i].x;
+    fb[i] = f[i].y;
+  }
+  if (SUMS) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float* fc = c ? fb : fa;
+      float f0 = E::get(E::put(fc[0]));
+      if (S != kF32) f0 += c ? phc.y : phc.x;  // slot 0 holds f_0 - phi
+      sums[4 * c] = f0 + ((E::get(E::put(fc[1])) + E::get(E::put(fc[2]))) +
+                          (E::get(E::put(fc[3])) + E::get(E::put(fc[4]))) +
+                          (E::get(E::put(fc[5])) + E::get(E::put(fc[6]))));
+    }
+  }
+  store_f<kAB, S>(dst, idx, na, fa);
+  store_f<kAB, S>(dst, idx2, nb2, fb);
 }
 
 // Sums of the fused step sums over the 32 cells of a warp, stored as 5 doubles at

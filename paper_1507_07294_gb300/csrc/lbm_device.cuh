@@ -36,6 +36,8 @@ struct Geometry {
   int storage;           // population storage type (Storage); selects the kernel instance
   int row_tiles;         // nx / kTile when rows are whole tiles and a plane of tiles spans
                          // < 2^31 bytes (pull addressing of RowPull), else 0
+  int pairs;             // 1: the two-array stream-collide takes two cells per thread
+                         // (k_collide2; needs row_tiles and nx a multiple of 2 kTile)
 };
 
 __device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
@@ -360,16 +362,104 @@ __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // ---------------------------------------------------------------------------------
+// Per-cell arithmetic, generic over the lane type V: float for one cell per thread,
+// float2 for two cells per thread (one in each lane, the paired FP32 instructions
+// __fadd2_rn, __fmul2_rn, __ffma2_rn doing both cells at once).  Every sum, product
+// and fused multiply-add is written with an explicit rounding intrinsic, which the
+// compiler never contracts or splits; each lane of a paired instruction rounds like
+// the scalar one.  So a cell's values are the same bits whichever kernel, lane type or
+// number of cells per thread computes them.
+// ---------------------------------------------------------------------------------
+template <typename V>
+struct VOps;
+
+template <>
+struct VOps<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float neg(float a) { return -a; }
+  static __device__ __forceinline__ float k(float a) { return a; }
+  static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+};
+
+template <>
+struct VOps<float2> {
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  // a - b as b * (-1) + a: the product is exact, so each lane rounds like a - b
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+  }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+  static __device__ __forceinline__ float2 k(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ float2 rcp(float2 a) {
+    return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+  }
+};
+
+// Stencil of one scalar field around the cell(s): centre, 6 faces, 8 corners.
+template <typename V>
+struct StencilV {
+  V c;                    // centre
+  V xm, xp, ym, yp, zm, zp;  // faces
+  V k[8];                 // corners, k[(sz > 0) * 4 + (sy > 0) * 2 + (sx > 0)]
+};
+typedef StencilV<float> Stencil;
+
+// The difference schemes with the D3Q7 weights (omega_i / c_s^2 = 1/2 for every A):
+// plain central differences on the 6 faces.
+template <typename V>
+__device__ __forceinline__ V stencil_lap7(const StencilV<V>& s) {
+  typedef VOps<V> O;
+  const V faces = O::add(O::add(O::add(s.xm, s.xp), O::add(s.ym, s.yp)), O::add(s.zm, s.zp));
+  return O::fma(O::k(-6.0f), s.c, faces);
+}
+
+template <typename V>
+__device__ __forceinline__ void stencil_grad7(const StencilV<V>& s, V g[3]) {
+  typedef VOps<V> O;
+  g[0] = O::mul(O::k(0.5f), O::sub(s.xp, s.xm));
+  g[1] = O::mul(O::k(0.5f), O::sub(s.yp, s.ym));
+  g[2] = O::mul(O::k(0.5f), O::sub(s.zp, s.zm));
+}
+
 // Isotropic difference schemes on the 15-point D3Q15 stencil (Eqs. 35-36 with the
 // flow-lattice weights 1/9 (faces), 1/72 (corners) and c_s^2 = 1/3):
-//   grad chi = 1/3 (face differences) + 1/24 (corner differences)
 //   lap chi  = 2/3 sum_faces (chi_n - chi) + 1/12 sum_corners (chi_n - chi)
-// ---------------------------------------------------------------------------------
-struct Stencil {
-  float c;                      // centre
-  float xm, xp, ym, yp, zm, zp; // faces
-  float k[8];                   // corners, k[(sz > 0) * 4 + (sy > 0) * 2 + (sx > 0)]
-};
+//   grad chi = 1/3 (face differences) + 1/24 (corner differences)
+template <typename V>
+__device__ __forceinline__ V stencil_lap(const StencilV<V>& s) {
+  typedef VOps<V> O;
+  const V faces = O::add(O::add(O::add(s.xm, s.xp), O::add(s.ym, s.yp)), O::add(s.zm, s.zp));
+  const V corners = O::add(O::add(O::add(s.k[0], s.k[1]), O::add(s.k[4], s.k[5])),
+                           O::add(O::add(s.k[2], s.k[3]), O::add(s.k[6], s.k[7])));
+  return O::fma(O::k(2.0f / 3.0f), O::fma(O::k(-6.0f), s.c, faces),
+                O::mul(O::k(1.0f / 12.0f), O::fma(O::k(-8.0f), s.c, corners)));
+}
+
+// Corner sums sum_corners c_a chi from the x differences and x sums of the four (y, z)
+// rows of corners.
+template <typename V>
+__device__ __forceinline__ void stencil_grad(const StencilV<V>& s, V g[3]) {
+  typedef VOps<V> O;
+  // rows of corners: (z-, y-) = k0, k1; (z-, y+) = k2, k3; (z+, y-) = k4, k5; (z+, y+) = k6, k7
+  const V dx0 = O::sub(s.k[1], s.k[0]), dx1 = O::sub(s.k[3], s.k[2]);
+  const V dx2 = O::sub(s.k[5], s.k[4]), dx3 = O::sub(s.k[7], s.k[6]);
+  const V sx0 = O::add(s.k[1], s.k[0]), sx1 = O::add(s.k[3], s.k[2]);
+  const V sx2 = O::add(s.k[5], s.k[4]), sx3 = O::add(s.k[7], s.k[6]);
+  const V kx = O::add(O::add(dx0, dx2), O::add(dx1, dx3));
+  const V ky = O::sub(O::add(sx1, sx3), O::add(sx0, sx2));
+  const V kz = O::add(O::sub(sx2, sx0), O::sub(sx3, sx1));
+  const V third = O::k(1.0f / 3.0f), w = O::k(1.0f / 24.0f);
+  g[0] = O::fma(w, kx, O::mul(third, O::sub(s.xp, s.xm)));
+  g[1] = O::fma(w, ky, O::mul(third, O::sub(s.yp, s.ym)));
+  g[2] = O::fma(w, kz, O::mul(third, O::sub(s.zp, s.zm)));
+}
 
 __device__ __forceinline__ void load_stencil(const float* __restrict__ a, int idx, const Nbr& nb,
                                              Stencil& s) {
@@ -387,45 +477,6 @@ __device__ __forceinline__ void load_stencil(const float* __restrict__ a, int id
     const int oz = (b & 4) ? nb.zp : nb.zm;
     s.k[b] = __ldg(a + idx + ox + oy + oz);
   }
-}
-
-// The same schemes with the D3Q7 weights (omega_i / c_s^2 = 1/2 for every A): plain
-// central differences on the 6 faces.
-__device__ __forceinline__ float stencil_lap7(const Stencil& s) {
-  return ((s.xm + s.xp) + (s.ym + s.yp) + (s.zm + s.zp)) - 6.0f * s.c;
-}
-
-__device__ __forceinline__ void stencil_grad7(const Stencil& s, float g[3]) {
-  g[0] = 0.5f * (s.xp - s.xm);
-  g[1] = 0.5f * (s.yp - s.ym);
-  g[2] = 0.5f * (s.zp - s.zm);
-}
-
-__device__ __forceinline__ float stencil_lap(const Stencil& s) {
-  const float2 fxy = padd(pr(s.xm, s.ym), pr(s.xp, s.yp));
-  const float faces = (fxy.x + fxy.y) + (s.zm + s.zp);
-  // (k0 + k1 + k4 + k5, k2 + k3 + k6 + k7)
-  const float2 c = padd(padd(pr(s.k[0], s.k[2]), pr(s.k[1], s.k[3])),
-                        padd(pr(s.k[4], s.k[6]), pr(s.k[5], s.k[7])));
-  const float corners = c.x + c.y;
-  return (2.0f / 3.0f) * (faces - 6.0f * s.c) + (1.0f / 12.0f) * (corners - 8.0f * s.c);
-}
-
-// Corner sums sum_corners c_a chi: the x differences and x sums of the four (y, z)
-// rows of corners, paired as (y-, y+) per z plane, then combined along y and z.
-__device__ __forceinline__ void stencil_grad(const Stencil& s, float g[3]) {
-  const float2 lo0 = pr(s.k[0], s.k[2]), hi0 = pr(s.k[1], s.k[3]);  // z- plane: x-, x+
-  const float2 lo1 = pr(s.k[4], s.k[6]), hi1 = pr(s.k[5], s.k[7]);  // z+ plane
-  const float2 dx = padd(psub(hi0, lo0), psub(hi1, lo1));  // x differences, (y-, y+)
-  const float2 sx0 = padd(hi0, lo0), sx1 = padd(hi1, lo1);  // x sums, (y-, y+) per plane
-  const float2 sy = padd(sx0, sx1);                          // (y- total, y+ total)
-  const float2 sz = psub(sx1, sx0);                          // z+ minus z-, (y-, y+)
-  const float kx = dx.x + dx.y, ky = sy.y - sy.x, kz = sz.x + sz.y;
-  const float2 gxy = pfma(pr(1.0f / 24.0f, 1.0f / 24.0f), pr(kx, ky),
-                          pmul(pr(1.0f / 3.0f, 1.0f / 3.0f), psub(pr(s.xp, s.yp), pr(s.xm, s.ym))));
-  g[0] = gxy.x;
-  g[1] = gxy.y;
-  g[2] = (1.0f / 3.0f) * (s.zp - s.zm) + (1.0f / 24.0f) * kz;
 }
 
 // u(x, t) of the interface-tracking tests at node (x, y, z) (nodes at integer
@@ -461,89 +512,122 @@ __device__ __forceinline__ void prescribed_velocity(const Physics& ph, const Geo
 
 // mu = 4 beta phi (phi^2 - 1) - kappa lap phi (Eq. 2).
 __device__ __forceinline__ float chemical_potential(const Physics& ph, float phi, float lap_phi) {
-  return 4.0f * ph.beta * phi * (phi * phi - 1.0f) - ph.kappa * lap_phi;
+  return __fmaf_rn(__fmul_rn(4.0f * ph.beta, phi), __fmaf_rn(phi, phi, -1.0f),
+                   __fmul_rn(-ph.kappa, lap_phi));
+}
+
+// The 15-point Laplacian of Eq. 36 at a node from per-plane partial sums of its column:
+// centres c0, c1, c2 of the planes below, at and above the node, the sum f1 of the 4
+// in-plane face neighbours at the node's plane, and the sums d0, d2 of the 4 in-plane
+// diagonal neighbours of the planes below and above (the stencil's corners):
+//   2/3 (faces - 6 c1) + 1/12 (corners - 8 c1)
+__device__ __forceinline__ float lap15_columns(float c0, float c1, float c2, float f1, float d0,
+                                               float d2) {
+  return __fmaf_rn(2.0f / 3.0f, __fmaf_rn(-6.0f, c1, __fadd_rn(f1, __fadd_rn(c0, c2))),
+                   __fmul_rn(1.0f / 12.0f, __fmaf_rn(-8.0f, c1, __fadd_rn(d0, d2))));
+}
+
+// The same with the D3Q7 weights: faces - 6 c1.
+__device__ __forceinline__ float lap7_columns(float c0, float c1, float c2, float f1) {
+  return __fmaf_rn(-6.0f, c1, __fadd_rn(f1, __fadd_rn(c0, c2)));
 }
 
 // ---------------------------------------------------------------------------------
-// Macroscopic state of one cell from its D3Q15 populations and the stencils.
+// Macroscopic state of the cell(s) from the D3Q15 populations and the stencils.
 // ---------------------------------------------------------------------------------
-struct Macro {
-  float rho, p;
-  float u[3];
-  float grad_rho[3];
-  float F[3];  // F_s + F_a + G
+template <typename V>
+struct MacroV {
+  V rho, p;
+  V u[3];
+  V grad_rho[3];
+  V F[3];  // F_s + F_a + G
 };
+typedef MacroV<float> Macro;
 
 // Moments of the D3Q15 populations (rows of Gamma, Eq. 25) and sum_{i != 0} g_i.
-struct Moments15 {
-  float m[15];
-  float moving;
+template <typename V>
+struct Moments15V {
+  V m[15];
+  V moving;
 };
+typedef Moments15V<float> Moments15;
 
-// The opposite pairs are taken as butterflies, two at a time: (1, 3) with (2, 4) gives
-// the x and y axes; the corners pair by c_y, (7, 9) | (8, 10) for c_y = +1 and
-// (11, 13) | (12, 14) for c_y = -1, and two more butterfly levels give their moments.
-__device__ __forceinline__ Moments15 moments15(const float g[15]) {
-  Moments15 r;
-  const float2 A = pr(g[1], g[3]), B = pr(g[2], g[4]);
-  const float2 s_xy = padd(A, B), d_xy = psub(A, B);  // (sx, sy), (dx, dy)
-  const float sz = g[5] + g[6], dz = g[5] - g[6];
-  const float2 c1 = pr(g[7], g[9]), c2 = pr(g[8], g[10]);
-  const float2 c3 = pr(g[11], g[13]), c4 = pr(g[12], g[14]);
-  const float2 sa_ = padd(c1, c2), da = psub(c1, c2);  // (s7, s9), (d7, d9)
-  const float2 sb = padd(c3, c4), db = psub(c3, c4);   // (s11, s13), (d11, d13)
-  const float2 sp = padd(sa_, sb), sm = psub(sa_, sb);  // (s7 + s11, s9 + s13), (s7 - s11, s9 - s13)
-  const float2 dp = padd(da, db), dm = psub(da, db);    // likewise for d
-  const float C = sp.x + sp.y;                          // sum over the 8 corners
-  const float2 Cxy = pr(dp.x + dp.y, dm.x + dm.y);      // sum c_x g, sum c_y g over corners
-  const float Cz = dp.x - dp.y;
-  const float sa = s_xy.x + s_xy.y + sz;
-  r.moving = sa + C;
-  r.m[0] = g[0] + sa + C;
-  r.m[1] = -2.0f * g[0] - sa + C;
-  r.m[2] = 16.0f * g[0] - 4.0f * sa + C;
-  const float2 m35 = padd(d_xy, Cxy), m46 = pfma(pr(-4.0f, -4.0f), d_xy, Cxy);
-  r.m[3] = m35.x;
-  r.m[4] = m46.x;
-  r.m[5] = m35.y;
-  r.m[6] = m46.y;
-  r.m[7] = dz + Cz;
-  r.m[8] = -4.0f * dz + Cz;
-  r.m[9] = 2.0f * s_xy.x - s_xy.y - sz;
-  r.m[10] = s_xy.y - sz;
-  r.m[11] = sm.x + sm.y;  // c_x c_y
-  r.m[12] = sm.x - sm.y;  // c_y c_z
-  r.m[13] = sp.x - sp.y;  // c_x c_z
-  r.m[14] = dm.x - dm.y;  // c_x c_y c_z
+// Opposite pairs as butterflies: axis sums and differences, the corners paired by
+// opposites and then by the sign of c_y.
+template <typename V>
+__device__ __forceinline__ Moments15V<V> moments15(const V g[15]) {
+  typedef VOps<V> O;
+  Moments15V<V> r;
+  const V sx = O::add(g[1], g[2]), dx = O::sub(g[1], g[2]);
+  const V sy = O::add(g[3], g[4]), dy = O::sub(g[3], g[4]);
+  const V sz = O::add(g[5], g[6]), dz = O::sub(g[5], g[6]);
+  const V s7 = O::add(g[7], g[8]), d7 = O::sub(g[7], g[8]);
+  const V s9 = O::add(g[9], g[10]), d9 = O::sub(g[9], g[10]);
+  const V s11 = O::add(g[11], g[12]), d11 = O::sub(g[11], g[12]);
+  const V s13 = O::add(g[13], g[14]), d13 = O::sub(g[13], g[14]);
+  const V spx = O::add(s7, s11), spy = O::add(s9, s13);  // c_y = +1 corners paired with c_y = -1
+  const V smx = O::sub(s7, s11), smy = O::sub(s9, s13);
+  const V dpx = O::add(d7, d11), dpy = O::add(d9, d13);
+  const V dmx = O::sub(d7, d11), dmy = O::sub(d9, d13);
+  const V C = O::add(spx, spy);   // sum over the 8 corners
+  const V Cx = O::add(dpx, dpy);  // sum c_x g over the corners
+  const V Cy = O::add(dmx, dmy);  // sum c_y g
+  const V Cz = O::sub(dpx, dpy);  // sum c_z g
+  const V sa = O::add(O::add(sx, sy), sz);
+  r.moving = O::add(sa, C);
+  r.m[0] = O::add(O::add(g[0], sa), C);
+  r.m[1] = O::add(O::fma(O::k(-2.0f), g[0], O::neg(sa)), C);
+  r.m[2] = O::add(O::fma(O::k(16.0f), g[0], O::mul(O::k(-4.0f), sa)), C);
+  r.m[3] = O::add(dx, Cx);
+  r.m[4] = O::fma(O::k(-4.0f), dx, Cx);
+  r.m[5] = O::add(dy, Cy);
+  r.m[6] = O::fma(O::k(-4.0f), dy, Cy);
+  r.m[7] = O::add(dz, Cz);
+  r.m[8] = O::fma(O::k(-4.0f), dz, Cz);
+  r.m[9] = O::sub(O::fma(O::k(2.0f), sx, O::neg(sy)), sz);
+  r.m[10] = O::sub(sy, sz);
+  r.m[11] = O::add(smx, smy);  // c_x c_y
+  r.m[12] = O::sub(smx, smy);  // c_y c_z
+  r.m[13] = O::sub(spx, spy);  // c_x c_z
+  r.m[14] = O::sub(dmx, dmy);  // c_x c_y c_z
   return r;
 }
 
 // Eqs. 14, 29, 30 and the forces of Eq. 28, from the moments of the populations.
-__device__ __forceinline__ Macro macroscopic(const Physics& ph, const Moments15& mo, float phi,
-                                             float mu, const float grad_phi[3], float lap_mu) {
-  Macro m;
-  m.rho = ph.rho_g + (1.0f + phi) * ph.half_drho;
-  // lattice momentum sum_i c_i g_i and sum_{i != 0} g_i
-  const float jx = mo.m[3], jy = mo.m[5], jz = mo.m[7];
-  const float sum_moving = mo.moving;
-  float Fsg[3];
+template <typename V>
+__device__ __forceinline__ MacroV<V> macroscopic(const Physics& ph, const Moments15V<V>& mo, V phi,
+                                                 V mu, const V grad_phi[3], V lap_mu) {
+  typedef VOps<V> O;
+  MacroV<V> m;
+  m.rho = O::fma(O::add(O::k(1.0f), phi), O::k(ph.half_drho), O::k(ph.rho_g));
+  const V j[3] = {mo.m[3], mo.m[5], mo.m[7]};  // lattice momentum sum_i c_i g_i
+  const V wrho = O::sub(m.rho, O::k(ph.rho_ref));
+  V Fsg[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    m.grad_rho[a] = ph.half_drho * grad_phi[a];
-    Fsg[a] = mu * grad_phi[a] + (m.rho - ph.rho_ref) * ph.gacc[a];  // F_s + G
+    m.grad_rho[a] = O::mul(O::k(ph.half_drho), grad_phi[a]);
+    Fsg[a] = O::fma(mu, grad_phi[a], O::mul(wrho, O::k(ph.gacc[a])));  // F_s + G
   }
-  const float fa = ph.half_drho * ph.mob * lap_mu;  // F_a = fa * u
-  const float inv = __fdividef(1.0f, m.rho - 0.5f * fa);
-  m.u[0] = (jx + 0.5f * Fsg[0]) * inv;
-  m.u[1] = (jy + 0.5f * Fsg[1]) * inv;
-  m.u[2] = (jz + 0.5f * Fsg[2]) * inv;
-  const float uu = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
-  const float udr = m.u[0] * m.grad_rho[0] + m.u[1] * m.grad_rho[1] + m.u[2] * m.grad_rho[2];
-  // c_s^2/(1 - omega_0) = 3/7; rho s_0(u) = -rho u^2 / 3
-  m.p = (3.0f / 7.0f) * (sum_moving + 0.5f * udr - m.rho * uu * (1.0f / 3.0f));
+  const V fa = O::mul(O::k(ph.half_drho * ph.mob), lap_mu);  // F_a = fa * u
+  const V inv = O::rcp(O::fma(O::k(-0.5f), fa, m.rho));
 #pragma unroll
-  for (int a = 0; a < 3; ++a) m.F[a] = Fsg[a] + fa * m.u[a];
+  for (int a = 0; a < 3; ++a) m.u[a] = O::mul(O::fma(O::k(0.5f), Fsg[a], j[a]), inv);
+  const V uu = O::fma(m.u[0], m.u[0], O::fma(m.u[1], m.u[1], O::mul(m.u[2], m.u[2])));
+  const V udr = O::fma(m.u[0], m.grad_rho[0],
+                       O::fma(m.u[1], m.grad_rho[1], O::mul(m.u[2], m.grad_rho[2])));
+  // c_s^2/(1 - omega_0) = 3/7; rho s_0(u) = -rho u^2 / 3
+  m.p = O::mul(O::k(3.0f / 7.0f),
+               O::fma(O::k(-1.0f / 3.0f), O::mul(m.rho, uu), O::fma(O::k(0.5f), udr, mo.moving)));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) m.F[a] = O::fma(fa, m.u[a], Fsg[a]);
   return m;
+}
+
+// lambda_9..13 = 1 / tau_g with nu = c_s^2 (tau_g - 1/2) (Eq. 33), nu linear in phi.
+template <typename V>
+__device__ __forceinline__ V viscous_rate(const Physics& ph, V phi) {
+  typedef VOps<V> O;
+  return O::rcp(O::fma(O::k(3.0f), O::fma(phi, O::k(ph.half_dnu), O::k(ph.nu_mid)), O::k(0.5f)));
 }
 
 // ---------------------------------------------------------------------------------
@@ -553,107 +637,113 @@ __device__ __forceinline__ Macro macroscopic(const Physics& ph, const Moments15&
 // that the small correction is what passes through the FP32 back-transform.
 // Gamma^{-1} = Gamma^T diag(1/|row_k|^2), |row|^2 = 15,18,360,10,40,10,40,10,40,12,4,8,8,8,8.
 // ---------------------------------------------------------------------------------
-template <bool SRT = false>
-__device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], const Moments15& mo,
-                                              const Macro& M, float lambda_visc) {
-  const float* m = mo.m;
+template <bool SRT, typename V>
+__device__ __forceinline__ void collide_d3q15(const Physics& ph, V g[15], const Moments15V<V>& mo,
+                                              const MacroV<V>& M, V lambda_visc) {
+  typedef VOps<V> O;
+  const V* m = mo.m;
+  const V rho = M.rho, p = M.p, ux = M.u[0], uy = M.u[1], uz = M.u[2];
+  const V uxx = O::mul(ux, ux), uyy = O::mul(uy, uy), uzz = O::mul(uz, uz);
+  const V ruu = O::mul(rho, O::add(O::add(uxx, uyy), uzz));
+  const V rux = O::mul(rho, ux), ruy = O::mul(rho, uy), ruz = O::mul(rho, uz);
+  // equilibrium moments, Eq. 31 (c = 1); rows 0 and 14 are 0
+  V meq[15];
+  meq[1] = O::fma(O::k(3.0f), p, ruu);
+  meq[2] = O::neg(O::fma(O::k(45.0f), p, O::mul(O::k(5.0f), ruu)));
+  meq[3] = rux;
+  meq[4] = O::mul(O::k(-7.0f / 3.0f), rux);
+  meq[5] = ruy;
+  meq[6] = O::mul(O::k(-7.0f / 3.0f), ruy);
+  meq[7] = ruz;
+  meq[8] = O::mul(O::k(-7.0f / 3.0f), ruz);
+  meq[9] = O::mul(rho, O::sub(O::fma(O::k(2.0f), uxx, O::neg(uyy)), uzz));
+  meq[10] = O::mul(rho, O::sub(uyy, uzz));
+  meq[11] = O::mul(rux, uy);
+  meq[12] = O::mul(ruy, uz);
+  meq[13] = O::mul(rux, uz);
 
-  // equilibrium moments, Eq. 31 (c = 1)
-  const float rho = M.rho, p = M.p, ux = M.u[0], uy = M.u[1], uz = M.u[2];
-  const float uu = ux * ux + uy * uy + uz * uz;
-  float meq[15];
-  meq[0] = 0.0f;
-  meq[1] = 3.0f * p + rho * uu;
-  meq[2] = -(45.0f * p + 5.0f * rho * uu);
-  meq[3] = rho * ux;
-  meq[4] = (-7.0f / 3.0f) * rho * ux;
-  meq[5] = rho * uy;
-  meq[6] = (-7.0f / 3.0f) * rho * uy;
-  meq[7] = rho * uz;
-  meq[8] = (-7.0f / 3.0f) * rho * uz;
-  meq[9] = rho * (2.0f * ux * ux - uy * uy - uz * uz);
-  meq[10] = rho * (uy * uy - uz * uz);
-  meq[11] = rho * ux * uy;
-  meq[12] = rho * uy * uz;
-  meq[13] = rho * ux * uz;
-  meq[14] = 0.0f;
-
-  // forcing moments, Eq. 32 (c = 1, X = c_s^2 grad rho)
-  const float Xx = M.grad_rho[0] * (1.0f / 3.0f), Xy = M.grad_rho[1] * (1.0f / 3.0f),
-              Xz = M.grad_rho[2] * (1.0f / 3.0f);
-  const float Fx = M.F[0], Fy = M.F[1], Fz = M.F[2];
-  const float Yx = Xx + Fx, Yy = Xy + Fy, Yz = Xz + Fz;
-  const float udX = ux * Xx + uy * Xy + uz * Xz;
-  const float udF = ux * Fx + uy * Fy + uz * Fz;
-  float mT[15];
-  mT[0] = 3.0f * udX;  // u . grad rho
-  mT[1] = -udX + 2.0f * udF;
-  mT[2] = -(7.0f * udX + 10.0f * udF);
+  // forcing moments, Eq. 32 (c = 1, X = c_s^2 grad rho, Y = X + F)
+  const V third = O::k(1.0f / 3.0f);
+  const V Xx = O::mul(M.grad_rho[0], third), Xy = O::mul(M.grad_rho[1], third),
+          Xz = O::mul(M.grad_rho[2], third);
+  const V Fx = M.F[0], Fy = M.F[1], Fz = M.F[2];
+  const V Yx = O::add(Xx, Fx), Yy = O::add(Xy, Fy), Yz = O::add(Xz, Fz);
+  const V udX = O::fma(ux, Xx, O::fma(uy, Xy, O::mul(uz, Xz)));
+  const V udF = O::fma(ux, Fx, O::fma(uy, Fy, O::mul(uz, Fz)));
+  const V uYx = O::mul(ux, Yx), uYy = O::mul(uy, Yy), uYz = O::mul(uz, Yz);
+  V mT[15];
+  mT[0] = O::mul(O::k(3.0f), udX);  // u . grad rho
+  mT[1] = O::fma(O::k(2.0f), udF, O::neg(udX));
+  mT[2] = O::neg(O::fma(O::k(7.0f), udX, O::mul(O::k(10.0f), udF)));
   mT[3] = Fx;
-  mT[4] = (-7.0f / 3.0f) * Fx;
+  mT[4] = O::mul(O::k(-7.0f / 3.0f), Fx);
   mT[5] = Fy;
-  mT[6] = (-7.0f / 3.0f) * Fy;
+  mT[6] = O::mul(O::k(-7.0f / 3.0f), Fy);
   mT[7] = Fz;
-  mT[8] = (-7.0f / 3.0f) * Fz;
-  mT[9] = 4.0f * ux * Yx - 2.0f * uy * Yy - 2.0f * uz * Yz;
-  mT[10] = 2.0f * uy * Yy - 2.0f * uz * Yz;
-  mT[11] = ux * Yy + uy * Yx;
-  mT[12] = uy * Yz + uz * Yy;
-  mT[13] = ux * Yz + uz * Yx;
-  mT[14] = 0.0f;
+  mT[8] = O::mul(O::k(-7.0f / 3.0f), Fz);
+  mT[9] = O::fma(O::k(4.0f), uYx, O::mul(O::k(-2.0f), O::add(uYy, uYz)));
+  mT[10] = O::mul(O::k(2.0f), O::sub(uYy, uYz));
+  mT[11] = O::fma(ux, Yy, O::mul(uy, Yx));
+  mT[12] = O::fma(uy, Yz, O::mul(uz, Yy));
+  mT[13] = O::fma(ux, Yz, O::mul(uz, Yx));
 
   // Delta_k / |row_k|^2; the fixed rates come divided by the norms
-  float a[15];
-  const float keep_visc = 1.0f - 0.5f * lambda_visc;
+  V a[15];
+  const V keep = O::fma(O::k(-0.5f), lambda_visc, O::k(1.0f));
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
-    if (SRT || (k >= 9 && k <= 13))
-      a[k] = (lambda_visc * (m[k] - meq[k]) - keep_visc * mT[k]) * (1.0f / norm15(k));
-    else
-      a[k] = ph.sg_a[k] * (m[k] - meq[k]) - ph.sg_b[k] * mT[k];
+    const V d = (k == 0 || k == 14) ? m[k] : O::sub(m[k], meq[k]);
+    const bool visc = SRT || (k >= 9 && k <= 13);
+    if (k == 14) {
+      a[k] = visc ? O::mul(O::mul(lambda_visc, d), O::k(1.0f / norm15(k)))
+                  : O::mul(O::k(ph.sg_a[k]), d);
+    } else if (visc) {
+      a[k] = O::mul(O::fma(lambda_visc, d, O::mul(O::neg(keep), mT[k])), O::k(1.0f / norm15(k)));
+    } else {
+      a[k] = O::fma(O::k(ph.sg_a[k]), d, O::mul(O::k(-ph.sg_b[k]), mT[k]));
+    }
   }
 
   // back transform: g_i -= sum_k Gamma_ki a_k
-  const float e_axis = a[0] - a[1] - 4.0f * a[2];
-  g[0] -= a[0] - 2.0f * a[1] + 16.0f * a[2];
+  const V e_axis = O::fma(O::k(-4.0f), a[2], O::sub(a[0], a[1]));
+  g[0] = O::sub(g[0], O::fma(O::k(16.0f), a[2], O::fma(O::k(-2.0f), a[1], a[0])));
   {
-    // axis v: g(+v) -= e_v + o_v, g(-v) -= e_v - o_v; x and y paired, then z
-    const float2 o_xy = pfma(pr(-4.0f, -4.0f), pr(a[4], a[6]), pr(a[3], a[5]));
-    const float2 e_xy = pr(e_axis + 2.0f * a[9], e_axis - a[9] + a[10]);
-    const float2 gp = psub(pr(g[1], g[3]), padd(e_xy, o_xy));
-    const float2 gm = psub(pr(g[2], g[4]), psub(e_xy, o_xy));
-    g[1] = gp.x;
-    g[3] = gp.y;
-    g[2] = gm.x;
-    g[4] = gm.y;
-    const float oz = a[7] - 4.0f * a[8], ez = e_axis - a[9] - a[10];
-    g[5] -= ez + oz;
-    g[6] -= ez - oz;
+    // axis v: g(+v) -= e_v + o_v, g(-v) -= e_v - o_v
+    const V ox = O::fma(O::k(-4.0f), a[4], a[3]), oy = O::fma(O::k(-4.0f), a[6], a[5]);
+    const V oz = O::fma(O::k(-4.0f), a[8], a[7]);
+    const V ex = O::fma(O::k(2.0f), a[9], e_axis);
+    const V em = O::sub(e_axis, a[9]);
+    const V ey = O::add(em, a[10]), ez = O::sub(em, a[10]);
+    g[1] = O::sub(g[1], O::add(ex, ox));
+    g[2] = O::sub(g[2], O::sub(ex, ox));
+    g[3] = O::sub(g[3], O::add(ey, oy));
+    g[4] = O::sub(g[4], O::sub(ey, oy));
+    g[5] = O::sub(g[5], O::add(ez, oz));
+    g[6] = O::sub(g[6], O::sub(ez, oz));
   }
   {
     // corner v = (vx, vy, vz): g(+v) -= even + odd, g(-v) -= even - odd, with
     // even = e0 + vx vy a11 + vy vz a12 + vx vz a13 and odd = vx px + vy py + vz pz +
-    // vx vy vz a14.  The corners with vx = 1 pair as (vz = +1, vz = -1): (7, 9) for
-    // vy = +1, (11, 13) for vy = -1; then
+    // vx vy vz a14.  For the corners with vx = 1:
     //   even = (e0 + vz a13) + vy (a11 + vz a12),  odd = (px + vz pz) + vy (py + vz a14)
-    const float e0 = a[0] + a[1] + a[2];
-    const float px = a[3] + a[4], py = a[5] + a[6], pz = a[7] + a[8];
-    const float2 P = pr(e0 + a[13], e0 - a[13]), Q = pr(a[11] + a[12], a[11] - a[12]);
-    const float2 R = pr(px + pz, px - pz), T = pr(py + a[14], py - a[14]);
-    const float2 e_up = padd(P, Q), e_dn = psub(P, Q);  // vy = +1, -1
-    const float2 o_up = padd(R, T), o_dn = psub(R, T);
-    const float2 g79 = psub(pr(g[7], g[9]), padd(e_up, o_up));
-    const float2 g810 = psub(pr(g[8], g[10]), psub(e_up, o_up));
-    const float2 g1113 = psub(pr(g[11], g[13]), padd(e_dn, o_dn));
-    const float2 g1214 = psub(pr(g[12], g[14]), psub(e_dn, o_dn));
-    g[7] = g79.x;
-    g[9] = g79.y;
-    g[8] = g810.x;
-    g[10] = g810.y;
-    g[11] = g1113.x;
-    g[13] = g1113.y;
-    g[12] = g1214.x;
-    g[14] = g1214.y;
+    const V e0 = O::add(O::add(a[0], a[1]), a[2]);
+    const V px = O::add(a[3], a[4]), py = O::add(a[5], a[6]), pz = O::add(a[7], a[8]);
+    const V Pp = O::add(e0, a[13]), Pm = O::sub(e0, a[13]);        // vz = +1, -1
+    const V Qp = O::add(a[11], a[12]), Qm = O::sub(a[11], a[12]);
+    const V Rp = O::add(px, pz), Rm = O::sub(px, pz);
+    const V Tp = O::add(py, a[14]), Tm = O::sub(py, a[14]);
+    const V eu7 = O::add(Pp, Qp), eu9 = O::add(Pm, Qm);  // vy = +1
+    const V ed11 = O::sub(Pp, Qp), ed13 = O::sub(Pm, Qm);  // vy = -1
+    const V ou7 = O::add(Rp, Tp), ou9 = O::add(Rm, Tm);
+    const V od11 = O::sub(Rp, Tp), od13 = O::sub(Rm, Tm);
+    g[7] = O::sub(g[7], O::add(eu7, ou7));
+    g[8] = O::sub(g[8], O::sub(eu7, ou7));
+    g[9] = O::sub(g[9], O::add(eu9, ou9));
+    g[10] = O::sub(g[10], O::sub(eu9, ou9));
+    g[11] = O::sub(g[11], O::add(ed11, od11));
+    g[12] = O::sub(g[12], O::sub(ed11, od11));
+    g[13] = O::sub(g[13], O::add(ed13, od13));
+    g[14] = O::sub(g[14], O::sub(ed13, od13));
   }
 }
 
@@ -661,64 +751,57 @@ __device__ __forceinline__ void collide_d3q15(const Physics& ph, float g[15], co
 // D3Q7 MRT collision in moment space (Eqs. 15, 17, 18):
 //   m+ = m - S (m - m^eq) + (I - S/2) mR,   f+ = M^{-1} m+
 // again applied as f+ = f - M^{-1} Delta; |row|^2 of M = 7, 2, 2, 2, 42, 12, 4.
-// ---------------------------------------------------------------------------------
 // With SHIFT0 (16-bit storage) f[0] is not read: f_0 = phi - sum_{i>0} f_i, so
 // m_0 = phi and m_4 = 6 phi - 7 sum_{i>0} f_i; on return f[0] holds f_0^+ - phi.
-// Every scalar product and sum here is written with an explicit rounding intrinsic
-// (__fmul_rn, __fadd_rn, __fsub_rn, __fmaf_rn), which the compiler never contracts or
-// splits, so the result is the same bits in every kernel that inlines it (left to
-// itself, the compiler fused different multiply-add pairs in different kernels).
-template <bool SHIFT0 = false>
-__device__ __forceinline__ void collide_d3q7(const Physics& ph, float f[7], float phi, float mu,
-                                             const float u[3], const float dphiu[3]) {
-  // x and y opposite pairs as paired butterflies, (1, 3) with (2, 4)
-  const float2 fp = pr(f[1], f[3]), fm = pr(f[2], f[4]);
-  const float2 s_xy = padd(fp, fm), d_xy = psub(fp, fm);
-  const float sz = __fadd_rn(f[5], f[6]);
-  const float smov = __fadd_rn(__fadd_rn(s_xy.x, s_xy.y), sz);
-  float m[7];
-  m[0] = SHIFT0 ? phi : __fadd_rn(f[0], smov);
-  m[1] = d_xy.x;
-  m[2] = d_xy.y;
-  m[3] = __fsub_rn(f[5], f[6]);
-  m[4] = SHIFT0 ? __fmaf_rn(6.0f, phi, __fmul_rn(-7.0f, smov)) : __fmaf_rn(6.0f, f[0], -smov);
-  m[5] = __fsub_rn(__fmaf_rn(2.0f, s_xy.x, -s_xy.y), sz);
-  m[6] = __fsub_rn(s_xy.y, sz);
-  // m - m^eq (Eq. 17); rows 0, 5, 6 have m^eq = phi, 0, 0
+// ---------------------------------------------------------------------------------
+template <bool SHIFT0, typename V>
+__device__ __forceinline__ void collide_d3q7(const Physics& ph, V f[7], V phi, V mu, const V u[3],
+                                             const V dphiu[3]) {
+  typedef VOps<V> O;
+  const V sx = O::add(f[1], f[2]), dx = O::sub(f[1], f[2]);
+  const V sy = O::add(f[3], f[4]), dy = O::sub(f[3], f[4]);
+  const V sz = O::add(f[5], f[6]);
+  const V smov = O::add(O::add(sx, sy), sz);
+  V m[7];
+  m[0] = SHIFT0 ? phi : O::add(f[0], smov);
+  m[1] = dx;
+  m[2] = dy;
+  m[3] = O::sub(f[5], f[6]);
+  m[4] = SHIFT0 ? O::fma(O::k(6.0f), phi, O::mul(O::k(-7.0f), smov))
+                : O::fma(O::k(6.0f), f[0], O::neg(smov));
+  m[5] = O::sub(O::fma(O::k(2.0f), sx, O::neg(sy)), sz);
+  m[6] = O::sub(sy, sz);
+  // m - m^eq (Eq. 17); rows 5, 6 have m^eq = 0
   const float k4 = __fmul_rn(__fmul_rn(21.0f, ph.A), ph.eta);
-  float d[7];
-  d[0] = __fsub_rn(m[0], phi);
-  d[1] = __fsub_rn(m[1], __fmul_rn(phi, u[0]));
-  d[2] = __fsub_rn(m[2], __fmul_rn(phi, u[1]));
-  d[3] = __fsub_rn(m[3], __fmul_rn(phi, u[2]));
-  d[4] = __fsub_rn(m[4], __fmaf_rn(-k4, mu, __fmul_rn(6.0f, phi)));
+  V d[7];
+  d[0] = O::sub(m[0], phi);
+  d[1] = O::sub(m[1], O::mul(phi, u[0]));
+  d[2] = O::sub(m[2], O::mul(phi, u[1]));
+  d[3] = O::sub(m[3], O::mul(phi, u[2]));
+  d[4] = O::sub(m[4], O::fma(O::k(-k4), mu, O::mul(O::k(6.0f), phi)));
   d[5] = m[5];
   d[6] = m[6];
   // b_k = [s_k (m_k - m_k^eq) - (1 - s_k/2) mR_k] / |M_k|^2 with mR of Eq. 18
-  float b[7];
+  V b[7];
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     if (k >= 1 && k <= 3)
-      b[k] = __fmaf_rn(ph.sf_a[k], d[k], __fmul_rn(-ph.sf_b[k], dphiu[k - 1]));
+      b[k] = O::fma(O::k(ph.sf_a[k]), d[k], O::mul(O::k(-ph.sf_b[k]), dphiu[k - 1]));
     else
-      b[k] = __fmul_rn(ph.sf_a[k], d[k]);
+      b[k] = O::mul(O::k(ph.sf_a[k]), d[k]);
   }
-  const float e = __fsub_rn(b[0], b[4]);
-  const float c0 = __fmaf_rn(6.0f, b[4], b[0]);
-  if (SHIFT0)
-    f[0] = -__fadd_rn(smov, c0);
-  else
-    f[0] = __fsub_rn(f[0], c0);
-  const float2 e_xy = pr(__fmaf_rn(2.0f, b[5], e), __fadd_rn(__fsub_rn(e, b[5]), b[6]));
-  const float2 b12 = pr(b[1], b[2]);
-  const float2 up = psub(fp, padd(e_xy, b12)), dn = psub(fm, psub(e_xy, b12));
-  f[1] = up.x;
-  f[3] = up.y;
-  f[2] = dn.x;
-  f[4] = dn.y;
-  const float ez = __fsub_rn(__fsub_rn(e, b[5]), b[6]);
-  f[5] = __fsub_rn(f[5], __fadd_rn(ez, b[3]));
-  f[6] = __fsub_rn(f[6], __fsub_rn(ez, b[3]));
+  const V e = O::sub(b[0], b[4]);
+  const V c0 = O::fma(O::k(6.0f), b[4], b[0]);
+  f[0] = SHIFT0 ? O::neg(O::add(smov, c0)) : O::sub(f[0], c0);
+  const V ex = O::fma(O::k(2.0f), b[5], e);
+  const V em = O::sub(e, b[5]);
+  const V ey = O::add(em, b[6]), ez = O::sub(em, b[6]);
+  f[1] = O::sub(f[1], O::add(ex, b[1]));
+  f[2] = O::sub(f[2], O::sub(ex, b[1]));
+  f[3] = O::sub(f[3], O::add(ey, b[2]));
+  f[4] = O::sub(f[4], O::sub(ey, b[2]));
+  f[5] = O::sub(f[5], O::add(ez, b[3]));
+  f[6] = O::sub(f[6], O::sub(ez, b[3]));
 }
 
 }  // namespace lbm

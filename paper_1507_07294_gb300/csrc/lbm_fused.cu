@@ -213,8 +213,7 @@ __global__ void __launch_bounds__(kFThreads, fused_min_blocks<S>())
         const float f1 = (P1[a][b - 1] + P1[a][b + 1]) + (P1[a - 1][b] + P1[a + 1][b]);
         const float d0 = (P0[a - 1][b - 1] + P0[a - 1][b + 1]) + (P0[a + 1][b - 1] + P0[a + 1][b + 1]);
         const float d2 = (P2[a - 1][b - 1] + P2[a - 1][b + 1]) + (P2[a + 1][b - 1] + P2[a + 1][b + 1]);
-        const float lap = (2.0f / 3.0f) * ((f1 + (c0 + c2)) - 6.0f * c1) +
-                          (1.0f / 12.0f) * ((d0 + d2) - 8.0f * c1);
+        const float lap = lap15_columns(c0, c1, c2, f1, d0, d2);
         Mq[i][j] = chemical_potential(ph, c1, lap);
       };
       mu_item(ty, tx + 1);

@@ -51,8 +51,8 @@ cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);
 cudaError_t launch_widen(const float* in, double* out, int n, cudaStream_t st);
 int reduce_parts(const Geometry& geo);
-// Resident blocks per SM of k_collide (kernel 0) or the order-parameter kernel (kernel 1:
-// k_phi_rows with rows, else k_phi); 0 on error.
+// Resident blocks per SM of k_collide (kernel 0), the order-parameter kernel (kernel 1:
+// k_phi_rows with rows, else k_phi) or k_collide2 (kernel 3); 0 on error.
 int resident_blocks_per_sm(int kernel, int storage, bool rows = false);
 cudaError_t launch_reduce(const float* src, const float* phi, double* partial, double* out,
                           const Geometry& geo, int pattern, bool with_g, cudaStream_t st);

@@ -264,6 +264,37 @@ __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
   collide_cell<P, VAR, S>(src, dst, phi, mu, geo, ph, have_prev, idx);
 }
 
+// k_collide with two cells per thread (collide_pair, the arithmetic in paired FP32
+// instructions): block b takes cells 256 b .. 256 b + 255 as 4 pairs of adjacent tiles of
+// one row; lane l of warp w the cells 256 b + 64 w + l and 256 b + 64 w + 32 + l.  Pattern
+// AB on grids with Geometry::pairs (n is then a multiple of 64, so a warp is wholly
+// inside or outside the grid).  With SUMS each warp leaves the sums of its two tiles in
+// parts, as k_collide_sums.
+template <int S>
+constexpr int collide2_min_blocks() {
+  return 4;
+}
+
+template <int VAR, int S, bool SUMS>
+__global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
+    k_collide2(const float* src, float* dst, const float* __restrict__ phi,
+               const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev,
+               double* __restrict__ parts) {
+  prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
+  const int idx = blockIdx.x * kBlock + (threadIdx.x >> 5) * (2 * kTile) + (threadIdx.x & 31);
+  if (idx >= geo.n) return;
+  if (SUMS) {
+    float s[8];
+    collide_pair<VAR, S, true>(src, dst, phi, mu, geo, ph, have_prev, idx, s);
+    const bool bad0 = !(isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3]));
+    const bool bad1 = !(isfinite(s[4]) && isfinite(s[5]) && isfinite(s[6]) && isfinite(s[7]));
+    warp_sums_store(s, bad0, parts, idx & ~31);
+    warp_sums_store(s + 4, bad1, parts, (idx + kTile) & ~31);
+  } else {
+    collide_pair<VAR, S, false>(src, dst, phi, mu, geo, ph, have_prev, idx, nullptr);
+  }
+}
+
 // Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
 // each warp leaves 5 doubles in parts[5 w ..] (w = its first cell / 32; warp_sums_store).
 // The 32 cells of a warp are summed in FP32 by a fixed butterfly (FP64 throughput on
@@ -310,8 +341,8 @@ __global__ void __launch_bounds__(kBlock) k_che(const float* src, float* dst,
   float dphiu[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float cur = phi_c * u[a];
-    dphiu[a] = have_prev ? cur - prev[a] : 0.0f;
+    const float cur = __fmul_rn(phi_c, u[a]);
+    dphiu[a] = have_prev ? __fsub_rn(cur, prev[a]) : 0.0f;
     dst[phiu_index<S>(idx, a)] = cur;
   }
   collide_d3q7<S != kF32>(ph, f, phi_c, mu_c, u, dphiu);
@@ -659,7 +690,10 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
   const unsigned blocks = blocks_for(geo.n);
 #define LBM_COLLIDE_P(S)                                                                    \
   {                                                                                         \
-    if (pattern == kAB)                                                                     \
+    if (pattern == kAB && geo.pairs)                                                        \
+      k_collide2<VAR, S, false><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,     \
+                                                               prev, nullptr);              \
+    else if (pattern == kAB)                                                                \
       k_collide<kAB, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);     \
     else if (pattern == kAAEven)                                                            \
       k_collide<kAAEven, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev); \
@@ -697,7 +731,17 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
                                 bool have_prev, double* parts, double* partial, double* out,
                                 cudaStream_t st) {
   const int prev = have_prev ? 1 : 0;
-  LBM_DISPATCH(geo, pattern, k_collide_sums, src, dst, phi, mu, geo, ph, prev, parts);
+  if (pattern == kAB && geo.pairs) {
+    const unsigned blocks = blocks_for(geo.n);
+    if (geo.storage == kF16)
+      k_collide2<0, kF16, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
+    else if (geo.storage == kBF16)
+      k_collide2<0, kBF16, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
+    else
+      k_collide2<0, kF32, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
+  } else {
+    LBM_DISPATCH(geo, pattern, k_collide_sums, src, dst, phi, mu, geo, ph, prev, parts);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_step_sums_final(parts, partial, out, geo, st);
@@ -765,6 +809,10 @@ int resident_blocks_per_sm(int kernel, int storage, bool rows) {
     e = storage == kF16    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi_rows<kF16>, kBlock, 0)
         : storage == kBF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi_rows<kBF16>, kBlock, 0)
                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_phi_rows<kF32>, kBlock, 0);
+  else if (kernel == 3)
+    e = storage == kF16    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide2<0, kF16, false>, kBlock / 2, 0)
+        : storage == kBF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide2<0, kBF16, false>, kBlock / 2, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide2<0, kF32, false>, kBlock / 2, 0);
   else if (kernel == 0)
     e = storage == kF16    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kF16>, kBlock, 0)
         : storage == kBF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_collide<kAB, 0, kBF16>, kBlock, 0)
