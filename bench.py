@@ -57,14 +57,25 @@ STEP_BYTES_PER_CELL = COLLIDE_BYTES_PER_CELL + (7 + 1) * 4 + (1 + 1) * 4  # + k_
 COLLIDE_BYTES_PER_CELL_16 = 2 * (22 * 2 + 12) + 8
 STEP_BYTES_PER_CELL_16 = COLLIDE_BYTES_PER_CELL_16 + (7 * 2 + 4 + 4) + 8
 
-# DRAM traffic of k_collide per cell from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum divided by the cells of the captured launch), valid only for
-# the kernel source it was taken on (hash of csrc/lbm_device.cuh, lbm_cells.cuh and
-# lbm_kernels.cu).
+# The one-kernel step (k_fused): the state read and written once (200 B in FP32); with
+# 16-bit populations 2 x (44 + 12) plus phi of the previous step read and the new phi
+# written (the slot-0 shift).
+FUSED_BYTES_PER_CELL = 2 * (22 + 3) * 4
+FUSED_BYTES_PER_CELL_16 = 2 * (22 * 2 + 12) + 8
+
+# DRAM traffic per cell of the dominant kernel from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the cells of the captured launch), valid only for the
+# kernel source it was taken on (hash of csrc/lbm_device.cuh, lbm_cells.cuh,
+# lbm_kernels.cu and lbm_fused.cu).  Captures of one launch on the 128 x 128 x 512 case
+# (8,388,608 cells), scaled by cells to the benchmark: the traffic of these kernels grows
+# in proportion to the cells.
 NCU_TRAFFIC = {
-    # 1704.7 MB per launch over 8,388,608 cells (ncu --set full on the 128x128x512
-    # case, scaled by cells to the benchmark)
-    "k_collide": {"bytes_per_cell": 203.22, "kernel_sha": "f0da994cbf15259d"},
+    # 917.7 MB read + 794.5 MB written
+    "k_collide2": {"bytes_per_cell": 204.11, "kernel_sha": "9eedce4801f0f8c6"},
+    # 536.9 MB + 432.8 MB
+    "k_collide2_fp16": {"bytes_per_cell": 115.61, "kernel_sha": "9eedce4801f0f8c6"},
+    # 1432.3 MB + 799.9 MB
+    "k_fused": {"bytes_per_cell": 266.10, "kernel_sha": "9eedce4801f0f8c6"},
 }
 
 WORKLOADS = {
@@ -77,7 +88,7 @@ WORKLOADS = {
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("lbm_device.cuh", "lbm_cells.cuh", "lbm_kernels.cu"):
+    for name in ("lbm_device.cuh", "lbm_cells.cuh", "lbm_kernels.cu", "lbm_fused.cu"):
         with open(os.path.join(ROOT, "paper_1507_07294_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -386,6 +397,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     solver = L.Solver(w, stream=stream.cuda_stream, pattern=args.pattern, storage=args.storage)
     ctx = solver.ctx
+    if not getattr(args, "cell_pairs", 1):
+        L.lbm_set_tuning(ctx, L.LBM_TUNE_CELL_PAIRS, 0)
+    single_pass = bool(getattr(args, "single_pass", False))
+    if single_pass:
+        L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED, 1)
 
     group = RankGroup(world, rank, "nccl")
 
@@ -401,7 +417,7 @@ def run_ours(args):
     solver.step(args.warmup)
     tuning = None
     if not args.no_tune:
-        tuning = tune.autotune(ctx)
+        tuning = (tune.autotune_fused if single_pass else tune.autotune)(ctx)
         torch.cuda.synchronize()
 
     # ---- device-timed region -------------------------------------------------
@@ -425,6 +441,9 @@ def run_ours(args):
                          "mean_ms": round(ms / max(n, 1), 5)}
     L.lbm_profile(ctx, False)
     sum_phi, _ = solver.reduce()  # the run stayed finite
+    pairs = L.lbm_get_tuning(ctx, L.LBM_TUNE_CELL_PAIRS) == 1
+    coll_name = ("k_fused" if L.lbm_get_tuning(ctx, L.LBM_TUNE_FUSED) == 1
+                 else "k_collide2" if pairs else "k_collide")
 
     cells = w.cells
     value = aggregate_mlups(cells, args.steps, world, elapsed_ms * 1e-3)
@@ -433,14 +452,15 @@ def run_ours(args):
     wide = args.storage == "fp32"
     coll_bytes = COLLIDE_BYTES_PER_CELL if wide else COLLIDE_BYTES_PER_CELL_16
     step_bytes = STEP_BYTES_PER_CELL if wide else STEP_BYTES_PER_CELL_16
+    if coll_name == "k_fused":  # the whole step: the state read and written once
+        coll_bytes = step_bytes = FUSED_BYTES_PER_CELL if wide else FUSED_BYTES_PER_CELL_16
     achieved = coll_bytes * cells / (coll_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
-    tr = NCU_TRAFFIC.get("k_collide" if wide else f"k_collide_{args.storage}")
+    tr = NCU_TRAFFIC.get(coll_name if wide else f"{coll_name}_{args.storage}")
     traffic = round(tr["bytes_per_cell"] * cells) if tr and tr.get("kernel_sha") == src_hash else None
 
     # ---- end-to-end region through the C ABI with host buffers ---------------
-    e2e = None
-    if not args.no_e2e:
+    def e2e_run(nsteps):
         phi_host = torch.empty(cells, dtype=torch.float64, pin_memory=True).numpy()
         phi_host[:] = w.phi0.reshape(-1)
         # page-locked result buffers, allocated once like a server's I/O buffers
@@ -462,7 +482,7 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         L.lbm_init_phi(ctx, phi_host)
-        for k in range(args.steps):
+        for k in range(nsteps):
             slot = k & 1
             if k >= 2:
                 check_sums(slot)
@@ -470,16 +490,23 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 sums_host[slot].copy_(sums_dev[slot], non_blocking=True)
                 arrived[slot].record(stream)
-        for k in range(max(0, args.steps - 2), args.steps):
+        for k in range(max(0, nsteps - 2), nsteps):
             check_sums(k & 1)
         out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P, out=outs)
         barrier()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         assert np.isfinite(out["phi"]).all()
-        e2e = {"value": round(aggregate_mlups(cells, args.steps, world, t_e2e), 3), "unit": UNIT,
-               "h2d_bytes_per_step": round(8 * cells / args.steps),
-               "d2h_bytes_per_step": round(5 * 8 + 5 * 8 * cells / args.steps),
-               "seconds": round(t_e2e, 4)}
+        return {"value": round(aggregate_mlups(cells, nsteps, world, t_e2e), 3), "unit": UNIT,
+                "h2d_bytes_per_step": round(8 * cells / nsteps),
+                "d2h_bytes_per_step": round(5 * 8 + 5 * 8 * cells / nsteps),
+                "steps": nsteps, "seconds": round(t_e2e, 4)}
+
+    e2e = None
+    e2e_sustained = None
+    if not args.no_e2e:
+        e2e = e2e_run(args.steps)
+        # the same over 1000 steps or more: the one upload and the one read-out amortised
+        e2e_sustained = e2e if args.steps >= 1000 else e2e_run(1000)
 
     # ---- reduced-precision storage variants (same workload and step count) ------
     variants = None
@@ -491,14 +518,17 @@ def run_ours(args):
         runs = [("fp16", "ab", "fp16"), ("bf16", "ab", "bf16")]
         if args.pattern == "ab":
             runs.append(("aa", "aa", "fp32"))  # in place: half the state memory
+            runs.append(("single_pass", "ab", "fp32"))  # one kernel per step (LBM_TUNE_FUSED)
         for name, pattern, storage in runs:
             wide_v = storage == "fp32"
             cb = COLLIDE_BYTES_PER_CELL if wide_v else COLLIDE_BYTES_PER_CELL_16
             sb = STEP_BYTES_PER_CELL if wide_v else STEP_BYTES_PER_CELL_16
             vs = L.Solver(w, stream=stream.cuda_stream, pattern=pattern, storage=storage)
+            if name == "single_pass":
+                L.lbm_set_tuning(vs.ctx, L.LBM_TUNE_FUSED, 1)
             vs.step(args.warmup)
             if not args.no_tune:
-                tune.autotune(vs.ctx)
+                vt = (tune.autotune_fused if name == "single_pass" else tune.autotune)(vs.ctx)
             L.lbm_profile(vs.ctx, True)
             barrier()
             v0 = torch.cuda.Event(enable_timing=True)
@@ -518,7 +548,19 @@ def run_ours(args):
                 "k_collide_bytes_per_cell": cb,
                 "k_collide_frac": round(cb * cells / (cmean * 1e-3) / 1e9 / peak, 4),
                 "step_bytes_per_cell": sb}
-            if pattern == "aa":
+            if not args.no_tune:
+                entry["tuning"] = {k: v["value"] for k, v in vt.items()}
+            if name == "single_pass":
+                entry["kernel"] = "k_fused"
+                entry["k_fused_ms"] = entry.pop("k_collide_ms")
+                entry["algorithmic_bytes_per_cell"] = 200
+                entry["hbm_frac_at_200_bytes"] = round(
+                    200 * cells / (cmean * 1e-3) / 1e9 / peak, 4)
+                for key in ("k_collide_bytes_per_cell", "k_collide_frac", "step_bytes_per_cell"):
+                    entry.pop(key)
+                entry["segment_planes"] = L.lbm_get_tuning(vs.ctx, L.LBM_TUNE_FUSED_SEGMENT)
+                pattern_variants[name] = entry
+            elif pattern == "aa":
                 for key, pat in (("context_gb", pattern), ("context_gb_ab", "ab")):
                     grid_p, params_p = L.params_from_workload(w, pat, storage)
                     entry[key] = round(L.lbm_memory_bytes(grid_p, params_p) / 1e9, 2)
@@ -549,7 +591,7 @@ def run_ours(args):
                 "config": config_dict(args, w, world),
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                              "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                             "kernel": "k_collide",
+                             "kernel": coll_name,
                              "bytes_per_cell": coll_bytes,
                              "peak_source": f"{peak_kind} HBM copy bandwidth"},
                 "step_bytes_per_cell": step_bytes,
@@ -559,8 +601,8 @@ def run_ours(args):
                 "tuning": {k: v["value"] for k, v in tuning.items()} if tuning else None,
                 "storage_variants": variants, "pattern_variants": pattern_variants,
                 "serving": serving,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
-                "gpu_launches": 3 * args.steps,
+                "cpu_baseline": cpu, "e2e": e2e, "e2e_sustained": e2e_sustained, "clocks": clock,
+                "gpu_launches": (1 if coll_name == "k_fused" else 3) * args.steps,
                 "sum_phi": sum_phi}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -579,6 +621,10 @@ def main(argv=None):
                     help="population storage: two arrays (ab) or in place (aa)")
     ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="population storage of the main run (arithmetic is FP32 in all)")
+    ap.add_argument("--single-pass", action="store_true",
+                    help="run the main leg with the one-kernel step (LBM_TUNE_FUSED)")
+    ap.add_argument("--cell-pairs", type=int, choices=(0, 1), default=1,
+                    help="two cells per thread in the stream-collide pass where it applies")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",

@@ -53,17 +53,26 @@ struct BatchTable {
 
 namespace {
 
-// Largest r with first[r] <= item (first[0] = 0, first[nruns] = total).
-__device__ __forceinline__ int find_run(const int* __restrict__ first, int nruns, int item) {
+// Largest r with first[r] <= item (first[0] = 0, first[nruns] = total); `first` is the
+// block's shared-memory copy of the prefix sums.
+__device__ __forceinline__ int find_run(const int* first, int nruns, int item) {
   int lo = 0, hi = nruns - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(first + mid) <= item)
+    if (first[mid] <= item)
       lo = mid;
     else
       hi = mid - 1;
   }
   return lo;
+}
+
+// The block's threads copy the nruns + 1 prefix sums into shared memory once, so that
+// each block's run lookups are a binary search in shared memory rather than a chain of
+// dependent global loads; the caller synchronises before the first lookup (seek does).
+__device__ __forceinline__ void load_firsts(const int* __restrict__ first, int nruns, int* s_first) {
+  for (int k = threadIdx.x + threadIdx.y * blockDim.x; k <= nruns; k += blockDim.x * blockDim.y)
+    s_first[k] = __ldg(first + k);
 }
 
 // The block's threads copy run r's descriptor into shared memory.
@@ -84,17 +93,16 @@ struct RunCursor {
   int end = 0;     // one past its last item
 };
 
-__device__ __forceinline__ void seek(const BatchTable* __restrict__ t,
-                                     const int* __restrict__ firsts, int item, RunCursor& c,
-                                     RunDesc& sd) {
+__device__ __forceinline__ void seek(const BatchTable* __restrict__ t, const int* s_first,
+                                     int nruns, int item, RunCursor& c, RunDesc& sd) {
   if (item < c.end) return;
-  const int r = find_run(firsts, t->nruns, item);
-  __syncthreads();  // the block is done with the previous descriptor
+  __syncthreads();  // the block is done with the previous descriptor (and s_first is loaded)
+  const int r = find_run(s_first, nruns, item);
   load_desc(t, r, sd);
   __syncthreads();
   c.r = r;
-  c.first = __ldg(firsts + r);
-  c.end = __ldg(firsts + r + 1);
+  c.first = s_first[r];
+  c.end = s_first[r + 1];
 }
 
 // Work items are blocks of kBlock cells (order parameter, stream-collide) or bricks
@@ -106,10 +114,12 @@ template <int S>
 __global__ void __launch_bounds__(kBlock) kb_phi(const BatchTable* __restrict__ t, int step,
                                                  int dist) {
   __shared__ RunDesc sd;
-  const int nitems = t->total_cells;
+  __shared__ int s_first[kMaxBatchRuns + 1];
+  const int nitems = t->total_cells, nruns = t->nruns;
+  if (blockIdx.x < nitems) load_firsts(t->cell_first, nruns, s_first);
   RunCursor c;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    seek(t, t->cell_first, item, c, sd);
+    seek(t, s_first, nruns, item, c, sd);
     const float* src = sd.state[(sd.parity + step) & 1];
     if (threadIdx.x == 0 && dist > 0 && item + dist < c.end)
       prefetch_cells<S, false>(src, nullptr, nullptr, sd.geo,
@@ -122,10 +132,12 @@ __global__ void __launch_bounds__(kBlock) kb_phi(const BatchTable* __restrict__ 
 __global__ void __launch_bounds__(kTX* kTY) kb_mu(const BatchTable* __restrict__ t, int step) {
   __shared__ RunDesc sd;
   __shared__ float tile[kHZ][kHY][kHX];
-  const int nitems = t->total_bricks;
+  __shared__ int s_first[kMaxBatchRuns + 1];
+  const int nitems = t->total_bricks, nruns = t->nruns;
+  if (blockIdx.x < nitems) load_firsts(t->brick_first, nruns, s_first);
   RunCursor c;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    seek(t, t->brick_first, item, c, sd);
+    seek(t, s_first, nruns, item, c, sd);
     const int local = item - c.first;
     const int nbx = (sd.geo.nx + kTX - 1) / kTX, nby = (sd.geo.ny + kTY - 1) / kTY;
     const int bx = local % nbx, rest = local / nbx;
@@ -138,10 +150,12 @@ template <int S>
 __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>()) kb_collide(
     const BatchTable* __restrict__ t, int step, int dist) {
   __shared__ RunDesc sd;
-  const int nitems = t->total_cells;
+  __shared__ int s_first[kMaxBatchRuns + 1];
+  const int nitems = t->total_cells, nruns = t->nruns;
+  if (blockIdx.x < nitems) load_firsts(t->cell_first, nruns, s_first);
   RunCursor c;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    seek(t, t->cell_first, item, c, sd);
+    seek(t, s_first, nruns, item, c, sd);
     const float* src = sd.state[(sd.parity + step) & 1];
     if (threadIdx.x == 0 && dist > 0 && item + dist < c.end)
       prefetch_cells<S, true>(src, sd.phi, sd.mu, sd.geo,

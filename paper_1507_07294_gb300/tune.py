@@ -1,7 +1,8 @@
 """Autotuning of launch parameters on a live run.
 
 The tuned parameters change only speed, never results: the L2 prefetch distances of
-the stream-collide and order-parameter kernels (lbm_set_tuning).  Each candidate is
+the stream-collide and order-parameter kernels, and for the single-pass step its planes
+per segment and prefetch distance in planes (lbm_set_tuning).  Each candidate is
 timed with the library's CUDA-event kernel profile over a few steps of the run itself,
 so tuning advances the simulation by (number of candidates) x (warm + steps) steps.
 """
@@ -12,7 +13,7 @@ from typing import Dict, Iterable, Optional
 from . import lbm as L
 
 # candidate distances as fractions of the default (one wave of resident blocks)
-DEFAULT_FRACTIONS = (0.0, 0.67, 0.83, 1.0, 1.17)
+DEFAULT_FRACTIONS = (0.0, 0.33, 0.5, 0.67, 0.83, 1.0, 1.17)
 
 
 def _time_kernel(ctx, kernel: int, steps: int, warm: int) -> float:
@@ -47,3 +48,22 @@ def tuning_steps(steps: int = 8, warm: int = 2, fractions: Optional[Iterable[flo
     """Number of time steps autotune() advances the run by."""
     n = len(set(fractions or DEFAULT_FRACTIONS))
     return 2 * n * (steps + warm)
+
+
+def autotune_fused(ctx, steps: int = 6, warm: int = 2,
+                   segments: Iterable[int] = (0, 16, 32, 64),
+                   prefetch: Iterable[int] = (0, 1, 2)) -> Dict[str, dict]:
+    """For the single-pass step (LBM_TUNE_FUSED): pick the planes per segment and the L2
+    prefetch distance in planes by timing the kernel on the live run."""
+    times = {}
+    for seg in segments:
+        L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED_SEGMENT, seg)
+        for pf in prefetch:
+            L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED_PREFETCH, pf)
+            times[(seg, pf)] = _time_kernel(ctx, L.KERNEL_COLLIDE, steps, warm)
+    seg, pf = min(times, key=times.get)
+    L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED_SEGMENT, seg)
+    L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED_PREFETCH, pf)
+    return {"fused_segment": {"value": L.lbm_get_tuning(ctx, L.LBM_TUNE_FUSED_SEGMENT)},
+            "fused_prefetch": {"value": pf,
+                               "ms": {f"{s}/{p}": round(t, 5) for (s, p), t in times.items()}}}
