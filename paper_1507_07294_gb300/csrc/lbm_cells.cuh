@@ -406,61 +406,19 @@ __device__ __forceinline__ void collide_cell(const float* src, float* dst,
 }
 
 // ------------------------------------------- two cells per thread, paired FP32 -------
-// The stream-collide body for cells idx and idx + kTile (the same lane of two adjacent
-// tiles of one row; pattern AB): loads and stores per cell, every arithmetic step once
-// for both cells in the two lanes of float2 (the generic per-cell math with V = float2),
-// which halves the arithmetic instructions.  Per lane the operations are those of the
-// one-cell body, so each cell gets the same bits.  With SUMS, sums[0..3] and sums[4..7]
-// receive the two cells' contributions (as collide_loaded).
-template <int VAR, int S, bool SUMS>
-__device__ __forceinline__ void collide_pair(const float* src, float* dst,
-                                             const float* __restrict__ phi,
-                                             const float* __restrict__ mu, const Geometry& geo,
-                                             const Physics& ph, int have_prev, int idx,
-                                             float* sums) {
+// The arithmetic of the stream-collide body for two cells, one in each lane of float2
+// (the generic per-cell math with V = float2): g and f hold the pulled populations (f[0]
+// unused with 16-bit storage), prev the phi u of the previous step, sp and sm the phi
+// and mu stencils.  On return g and f hold the post-collision populations (with 16-bit
+// storage f[0] = f_0+ - phi) and cur the new phi u.  Per lane the operations are those
+// of the one-cell body, so each cell gets the same bits.
+template <int VAR, int S>
+__device__ __forceinline__ void pair_compute(const Physics& ph, int have_prev, float2 g[15],
+                                             float2 f[7], const float2 prev[3],
+                                             const StencilV<float2>& sp,
+                                             const StencilV<float2>& sm, float2 cur[3]) {
   typedef VOps<float2> O;
   constexpr bool D3Q7 = (VAR & kVarD3Q7) != 0;
-  int x, y, z;
-  cell_coords(geo, idx, x, y, z);
-  const int idx2 = idx + kTile;
-  const Nbr na = make_nbr(geo, x, y, z), nb2 = make_nbr(geo, x + kTile, y, z);
-  float ga[15], fa[7], pa[3], gb[15], fb[7], pb[3];
-  load_cell<kAB, S, true>(src, geo, idx, na, ga, fa, pa);
-  load_cell<kAB, S, true>(src, geo, idx2, nb2, gb, fb, pb);
-  StencilV<float2> sp, sm;
-  {
-    Stencil s0, s1;
-    load_stencil(phi, idx, na, s0);
-    load_stencil(phi, idx2, nb2, s1);
-    sp.c = make_float2(s0.c, s1.c);
-    sp.xm = make_float2(s0.xm, s1.xm);
-    sp.xp = make_float2(s0.xp, s1.xp);
-    sp.ym = make_float2(s0.ym, s1.ym);
-    sp.yp = make_float2(s0.yp, s1.yp);
-    sp.zm = make_float2(s0.zm, s1.zm);
-    sp.zp = make_float2(s0.zp, s1.zp);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sp.k[k] = make_float2(s0.k[k], s1.k[k]);
-  }
-  {
-    Stencil s0, s1;
-    load_stencil(mu, idx, na, s0);
-    load_stencil(mu, idx2, nb2, s1);
-    sm.c = make_float2(s0.c, s1.c);
-    sm.xm = make_float2(s0.xm, s1.xm);
-    sm.xp = make_float2(s0.xp, s1.xp);
-    sm.ym = make_float2(s0.ym, s1.ym);
-    sm.yp = make_float2(s0.yp, s1.yp);
-    sm.zm = make_float2(s0.zm, s1.zm);
-    sm.zp = make_float2(s0.zp, s1.zp);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sm.k[k] = make_float2(s0.k[k], s1.k[k]);
-  }
-  float2 g[15], f[7];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) g[i] = make_float2(ga[i], gb[i]);
-#pragma unroll
-  for (int i = 0; i < 7; ++i) f[i] = make_float2(fa[i], fb[i]);
   float2 grad_phi[3];
   if (D3Q7)
     stencil_grad7(sp, grad_phi);
@@ -472,31 +430,102 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
   const MacroV<float2> M = macroscopic(ph, mo, phc, muc, grad_phi, lap_mu);
   const float2 lambda_visc = viscous_rate(ph, phc);
   collide_d3q15<(VAR & kVarSrtFlow) != 0>(ph, g, mo, M, lambda_visc);
+  // d_t(phi u) by the backward difference of Eq. 34
+  float2 dphiu[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cur[a] = O::mul(phc, M.u[a]);
+    dphiu[a] = have_prev ? O::sub(cur[a], prev[a]) : make_float2(0.0f, 0.0f);
+  }
+  collide_d3q7<S != kF32>(ph, f, phc, muc, M.u, dphiu);
+}
+
+// Both stencils of one scalar field for cells idx and idx + kTile, packed per lane.
+__device__ __forceinline__ StencilV<float2> pair_stencil(const float* __restrict__ a, int idx0,
+                                                         const Nbr& n0, int idx1, const Nbr& n1) {
+  Stencil s0, s1;
+  load_stencil(a, idx0, n0, s0);
+  load_stencil(a, idx1, n1, s1);
+  StencilV<float2> sp;
+  sp.c = make_float2(s0.c, s1.c);
+  sp.xm = make_float2(s0.xm, s1.xm);
+  sp.xp = make_float2(s0.xp, s1.xp);
+  sp.ym = make_float2(s0.ym, s1.ym);
+  sp.yp = make_float2(s0.yp, s1.yp);
+  sp.zm = make_float2(s0.zm, s1.zm);
+  sp.zp = make_float2(s0.zp, s1.zp);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sp.k[k] = make_float2(s0.k[k], s1.k[k]);
+  return sp;
+}
+
+// Post-collision sums of one cell (lane c of the pair) as collide_loaded forms them:
+// sum phi and the lattice momentum with the wall reversal, each value as the next step
+// reads it back from storage.
+template <int S>
+__device__ __forceinline__ void pair_sums(const float2 g[15], const float2 f[7], float2 phc,
+                                          const Nbr& nb, int c, float* sums) {
   typedef Elem<S> E;
-  if (SUMS) {
+  float v[15];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      float v[15];
-#pragma unroll
-      for (int i = 0; i < 15; ++i) v[i] = E::get(E::put(c ? g[i].y : g[i].x));
-      const float a7 = v[7] - v[8], a9 = v[9] - v[10], a11 = v[11] - v[12], a13 = v[13] - v[14];
-      float jx = (v[1] - v[2]) + ((a7 + a9) + (a11 + a13));
-      float jy = (v[3] - v[4]) + ((a7 + a9) - (a11 + a13));
-      float jz = (v[5] - v[6]) + ((a7 - a9) + (a11 - a13));
-      if (na.wlo || na.whi) {
+  for (int i = 0; i < 15; ++i) v[i] = E::get(E::put(c ? g[i].y : g[i].x));
+  const float a7 = v[7] - v[8], a9 = v[9] - v[10], a11 = v[11] - v[12], a13 = v[13] - v[14];
+  float jx = (v[1] - v[2]) + ((a7 + a9) + (a11 + a13));
+  float jy = (v[3] - v[4]) + ((a7 + a9) - (a11 + a13));
+  float jz = (v[5] - v[6]) + ((a7 - a9) + (a11 - a13));
+  if (nb.wlo || nb.whi) {
 #define X(I, O_, CX, CY, CZ)                                   \
-  if ((CZ > 0 && na.whi) || (CZ < 0 && na.wlo)) {              \
+  if ((CZ > 0 && nb.whi) || (CZ < 0 && nb.wlo)) {              \
     jx -= 2.0f * CX * v[I];                                    \
     jy -= 2.0f * CY * v[I];                                    \
     jz -= 2.0f * CZ * v[I];                                    \
   }
-        LBM_D3Q15_LIST(X)
+    LBM_D3Q15_LIST(X)
 #undef X
-      }
-      sums[4 * c + 1] = jx;
-      sums[4 * c + 2] = jy;
-      sums[4 * c + 3] = jz;
-    }
+  }
+  sums[1] = jx;
+  sums[2] = jy;
+  sums[3] = jz;
+  float fc[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) fc[i] = c ? f[i].y : f[i].x;
+  float f0 = E::get(E::put(fc[0]));
+  if (S != kF32) f0 += c ? phc.y : phc.x;  // slot 0 holds f_0 - phi
+  sums[0] = f0 + ((E::get(E::put(fc[1])) + E::get(E::put(fc[2]))) +
+                  (E::get(E::put(fc[3])) + E::get(E::put(fc[4]))) +
+                  (E::get(E::put(fc[5])) + E::get(E::put(fc[6]))));
+}
+
+// The stream-collide body for cells idx and idx + kTile (the same lane of two adjacent
+// tiles of one row; pattern AB): loads and stores per cell, the arithmetic once for both
+// (pair_compute).  With SUMS, sums[0..3] and sums[4..7] receive the two cells'
+// contributions (as collide_loaded).
+template <int VAR, int S, bool SUMS>
+__device__ __forceinline__ void collide_pair(const float* src, float* dst,
+                                             const float* __restrict__ phi,
+                                             const float* __restrict__ mu, const Geometry& geo,
+                                             const Physics& ph, int have_prev, int idx,
+                                             float* sums) {
+  int x, y, z;
+  cell_coords(geo, idx, x, y, z);
+  const int idx2 = idx + kTile;
+  const Nbr na = make_nbr(geo, x, y, z), nb2 = make_nbr(geo, x + kTile, y, z);
+  float ga[15], fa[7], pa[3], gb[15], fb[7], pb[3];
+  load_cell<kAB, S, true>(src, geo, idx, na, ga, fa, pa);
+  load_cell<kAB, S, true>(src, geo, idx2, nb2, gb, fb, pb);
+  const StencilV<float2> sp = pair_stencil(phi, idx, na, idx2, nb2);
+  const StencilV<float2> sm = pair_stencil(mu, idx, na, idx2, nb2);
+  float2 g[15], f[7], prev[3], cur[3];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) g[i] = make_float2(ga[i], gb[i]);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i] = make_float2(fa[i], fb[i]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) prev[a] = make_float2(pa[a], pb[a]);
+  pair_compute<VAR, S>(ph, have_prev, g, f, prev, sp, sm, cur);
+  if (SUMS) {
+    pair_sums<S>(g, f, sp.c, na, 0, sums);
+    pair_sums<S>(g, f, sp.c, nb2, 1, sums + 4);
   }
 #pragma unroll
   for (int i = 0; i < 15; ++i) {
@@ -505,31 +534,15 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
   }
   store_g<kAB, S>(dst, idx, na, ga);
   store_g<kAB, S>(dst, idx2, nb2, gb);
-  // d_t(phi u) by the backward difference of Eq. 34; phi u lives in the own tile
-  float2 dphiu[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float2 cur = O::mul(phc, M.u[a]);
-    dphiu[a] = have_prev ? O::sub(cur, make_float2(pa[a], pb[a])) : make_float2(0.0f, 0.0f);
-    dst[phiu_index<S>(idx, a)] = cur.x;
-    dst[phiu_index<S>(idx2, a)] = cur.y;
+    dst[phiu_index<S>(idx, a)] = cur[a].x;
+    dst[phiu_index<S>(idx2, a)] = cur[a].y;
   }
-  collide_d3q7<S != kF32>(ph, f, phc, muc, M.u, dphiu);
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     fa[i] = f[i].x;
     fb[i] = f[i].y;
-  }
-  if (SUMS) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const float* fc = c ? fb : fa;
-      float f0 = E::get(E::put(fc[0]));
-      if (S != kF32) f0 += c ? phc.y : phc.x;  // slot 0 holds f_0 - phi
-      sums[4 * c] = f0 + ((E::get(E::put(fc[1])) + E::get(E::put(fc[2]))) +
-                          (E::get(E::put(fc[3])) + E::get(E::put(fc[4]))) +
-                          (E::get(E::put(fc[5])) + E::get(E::put(fc[6]))));
-    }
   }
   store_f<kAB, S>(dst, idx, na, fa);
   store_f<kAB, S>(dst, idx2, nb2, fb);
