@@ -146,8 +146,12 @@ __global__ void __launch_bounds__(kTX* kTY) kb_mu(const BatchTable* __restrict__
   }
 }
 
+// Blocks of kBlock / 2 threads take items of kBlock cells: two cells per thread, in the
+// two lanes of paired instructions (collide_pair: cells x and x + 32 of a row) for runs
+// whose rows are pairs of tiles (Geometry::pairs), else one after the other with the
+// one-cell body (cells i and i + kBlock / 2 of the item).  Bit-identical either way.
 template <int S>
-__global__ void __launch_bounds__(kBlock, collide_min_blocks<S>()) kb_collide(
+__global__ void __launch_bounds__(kBlock / 2, 4) kb_collide(
     const BatchTable* __restrict__ t, int step, int dist) {
   __shared__ RunDesc sd;
   __shared__ int s_first[kMaxBatchRuns + 1];
@@ -160,10 +164,21 @@ __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>()) kb_collide(
     if (threadIdx.x == 0 && dist > 0 && item + dist < c.end)
       prefetch_cells<S, true>(src, sd.phi, sd.mu, sd.geo,
                               static_cast<long long>(item + dist - c.first) * kBlock);
-    const int idx = (item - c.first) * kBlock + threadIdx.x;
-    if (idx < sd.geo.n)
-      collide_cell<kAB, 0, S>(src, sd.state[(sd.parity + step + 1) & 1], sd.phi, sd.mu, sd.geo,
-                              sd.ph, sd.have_prev, idx);
+    float* dst = sd.state[(sd.parity + step + 1) & 1];
+    const int base = (item - c.first) * kBlock;
+    if (sd.geo.pairs) {
+      const int idx = base + (threadIdx.x >> 5) * (2 * kTile) + (threadIdx.x & 31);
+      if (idx < sd.geo.n)
+        collide_pair<0, S, false>(src, dst, sd.phi, sd.mu, sd.geo, sd.ph, sd.have_prev, idx,
+                                  nullptr);
+    } else {
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int idx = base + h * (kBlock / 2) + threadIdx.x;
+        if (idx < sd.geo.n)
+          collide_cell<kAB, 0, S>(src, dst, sd.phi, sd.mu, sd.geo, sd.ph, sd.have_prev, idx);
+      }
+    }
   }
 }
 
@@ -235,11 +250,11 @@ cudaError_t launch_pass_kernels(lbm_batch* b, int storage, int steps) {
       lbm::kb_phi<lbm::kF32><<<g[0], lbm::kBlock, 0, b->stream>>>(t, s, d[0]);
     lbm::kb_mu<<<g[1], dim3(lbm::kTX, lbm::kTY), 0, b->stream>>>(t, s);
     if (storage == LBM_STORAGE_FP16)
-      lbm::kb_collide<lbm::kF16><<<g[2], lbm::kBlock, 0, b->stream>>>(t, s, d[2]);
+      lbm::kb_collide<lbm::kF16><<<g[2], lbm::kBlock / 2, 0, b->stream>>>(t, s, d[2]);
     else if (storage == LBM_STORAGE_BF16)
-      lbm::kb_collide<lbm::kBF16><<<g[2], lbm::kBlock, 0, b->stream>>>(t, s, d[2]);
+      lbm::kb_collide<lbm::kBF16><<<g[2], lbm::kBlock / 2, 0, b->stream>>>(t, s, d[2]);
     else
-      lbm::kb_collide<lbm::kF32><<<g[2], lbm::kBlock, 0, b->stream>>>(t, s, d[2]);
+      lbm::kb_collide<lbm::kF32><<<g[2], lbm::kBlock / 2, 0, b->stream>>>(t, s, d[2]);
   }
   return cudaGetLastError();
 }
@@ -306,7 +321,7 @@ lbm_status lbm_batch_create(const lbm_allocator* alloc, void* cuda_stream, lbm_b
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->resident[1], lbm::kb_mu, lbm::kTX * lbm::kTY,
                                                 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->resident[2], lbm::kb_collide<lbm::kF32>,
-                                                lbm::kBlock, 0);
+                                                lbm::kBlock / 2, 0);
   for (int p = 0; p < 3; ++p) b->resident[p] = std::max(b->resident[p], 1);
   b->grid[0] = b->sms * 8;
   b->grid[1] = b->sms * 6;

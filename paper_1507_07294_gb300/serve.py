@@ -430,7 +430,7 @@ def tune_batch(engine: GpuEngine, grids: Sequence[Tuple[int, int, int]], quantum
     torch = engine.torch
     b = engine.batch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    wave = sms * 3 * 256  # cells of one wave of stream-collide blocks
+    wave = sms * 4 * 256  # cells of one wave of stream-collide blocks (4 per SM, 256 cells each)
     runs = [engine.open(Request(-1, 0.0, tuple(g), 1000.0, 0.5, 5e-3, 1)) for g in grids]
     for s in runs:
         s.step(1)
@@ -448,8 +448,8 @@ def tune_batch(engine: GpuEngine, grids: Sequence[Tuple[int, int, int]], quantum
 
     knobs = [
         ("split_cells", b.set_split, [0] + [k * wave for k in (1, 2, 4, 8, 16)]),
-        ("collide_blocks", lambda v: b.set_grid(2, v), [0, 3 * sms, 6 * sms]),
-        ("collide_prefetch", lambda v: b.set_prefetch(2, v), [-1, 0, sms * 3 // 2]),
+        ("collide_blocks", lambda v: b.set_grid(2, v), [0, 4 * sms, 8 * sms]),
+        ("collide_prefetch", lambda v: b.set_prefetch(2, v), [-1, 0, sms * 2]),
         ("phi_blocks", lambda v: b.set_grid(0, v), [0, 8 * sms, 16 * sms]),
         ("mu_blocks", lambda v: b.set_grid(1, v), [0, 6 * sms, 12 * sms]),
     ]
