@@ -52,6 +52,7 @@ struct lbm_ctx {
   long long tma_polls = -1;  // poll budget of the copy's wait; -1: the kernel default
   int row_tiles = 0;         // Geometry::row_tiles when LBM_TUNE_ROWS is on
   int pairs = 0;             // Geometry::pairs when LBM_TUNE_CELL_PAIRS is on
+  int stage_rows = 0;        // Geometry::stage when LBM_TUNE_STENCIL_STAGE is on
 
   // single-pass step (lbm_fused.cu): enabled, planes per segment (0: by grid size), L2
   // prefetch distance in planes
@@ -435,7 +436,9 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
                                                          pat, prev, c->step_parts, c->partial,
                                                          sums_out, c->stream)
                              : lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat,
-                                                   prev, c->stream);
+                                                   prev, c->stream, error_word(c),
+                                                   c->tma_polls < 0 ? lbm::mu_tma_default_polls()
+                                                                    : c->tma_polls);
            }));
   } else {
     const float tf = velocity_time_factor(c, c->step);
@@ -549,6 +552,8 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   // two cells per thread in the two-array stream-collide: cells x and x + 32 of one row
   if (params->pattern == LBM_PATTERN_AB && grid->nx % (2 * lbm::kTile) == 0) c->pairs = 1;
   c->geo.pairs = c->pairs;
+  if (c->pairs && lbm::stage_shape_ok(c->geo)) c->stage_rows = 1;
+  c->geo.stage = c->stage_rows;
   // L2 prefetch distances: one wave of resident blocks
   {
     int dev = 0, sms = 0;
@@ -866,6 +871,10 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_CELL_PAIRS takes 0 or 1");
       c->geo.pairs = value == 1 ? c->pairs : 0;
       break;
+    case LBM_TUNE_STENCIL_STAGE:
+      if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_STENCIL_STAGE takes 0 or 1");
+      c->geo.stage = value == 1 ? c->stage_rows : 0;
+      break;
     case LBM_TUNE_FUSED:
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_FUSED takes 0 or 1");
       c->use_fused = value == 1;
@@ -899,6 +908,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
       *value = c->geo.row_tiles > 0 ? 1 : 0;
       return LBM_OK;
     case LBM_TUNE_CELL_PAIRS: *value = c->geo.pairs; return LBM_OK;
+    case LBM_TUNE_STENCIL_STAGE: *value = (c->geo.pairs && c->geo.stage) ? 1 : 0; return LBM_OK;
     case LBM_TUNE_FUSED: *value = fused_applies(c) ? 1 : 0; return LBM_OK;
     case LBM_TUNE_FUSED_SEGMENT: *value = fused_segment(c); return LBM_OK;
     case LBM_TUNE_FUSED_PREFETCH: *value = c->fused_pf; return LBM_OK;

@@ -32,9 +32,14 @@ long long mu_tma_default_polls();
 bool mu_tma_shape_ok(const Geometry& geo);
 // TMA box of the chemical-potential pass: (kTX + 8, kTY + 2, kTZ + 2)
 constexpr unsigned kMuTmaBox[3] = {40, 10, 18};
+// With err non-null and Geometry::stage set, the two-cell pass stages its stencils in
+// shared memory by TMA bulk copies (k_collide2t), with a wait bounded by `polls` whose
+// failure sets *err like launch_mu_tma.
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
                            const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
-                           cudaStream_t st);
+                           cudaStream_t st, int* err = nullptr, long long polls = 0);
+// Grids whose rows k_collide2t can stage (nx of 64, 128 or 256).
+bool stage_shape_ok(const Geometry& geo);
 cudaError_t launch_che(const float* src, float* dst, const float* phi, const float* mu,
                        const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
                        float tf, cudaStream_t st);

@@ -297,6 +297,166 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
   }
 }
 
+// k_collide2 with the phi and mu stencils staged in shared memory by TMA bulk copies
+// (grids whose rows are 64, 128 or 256 cells: a block's 256 cells are R = 256 / nx whole
+// rows).  For each of its rows and each of the 9 (dy, dz) neighbour rows the stencils
+// use (walls: the ghost of a row beyond the wall is the row itself), thread 0 issues one
+// `cp.async.bulk` of the whole row of phi and one of mu into shared memory (at most 72
+// copies of nx floats, completing on one mbarrier), while every thread loads its two
+// cells' populations; after the (bounded) wait the two x-halo values of each row are
+// filled from the row itself (periodic x) and the cells read their 15-point stencils
+// from shared memory: no stencil load instructions and no stencil registers in flight.
+// The values are those load_stencil reads, so the state is bit-identical to k_collide2.
+// A block whose wait runs out waits once more (bounded), sets *err as k_mu_tma does,
+// and returns without touching the state.
+constexpr int kStRowPad = 8;                            // floats: 4 before, 4 after a row
+constexpr int kStFloats = 9 * 4 * (64 + kStRowPad);    // per field, max over nx = 64..256
+
+__device__ __forceinline__ void bulk_row(unsigned dst, const float* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+template <int VAR, int S>
+__global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
+    k_collide2t(const float* src, float* dst, const float* __restrict__ phi,
+                const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev, int* err,
+                long long polls) {
+  __shared__ alignas(128) float st[2][kStFloats];
+  __shared__ alignas(8) unsigned long long bar_storage;
+  prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
+  const unsigned bar = smem_addr(&bar_storage);
+  const int nx = geo.nx, R = kBlock / nx, stride = nx + kStRowPad;
+  const int b0 = blockIdx.x * kBlock;
+  const int rows = min(R, (geo.n - b0) / nx);  // whole rows of this block
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const unsigned row_bytes = static_cast<unsigned>(nx) * 4u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(2u * 9u * static_cast<unsigned>(rows) * row_bytes)
+                 : "memory");
+    for (int r = 0; r < rows; ++r) {
+      const int gr = b0 / nx + r;  // global row index: y + ny z
+      const int z = gr / geo.ny, y = gr - z * geo.ny;
+      for (int k = 0; k < 9; ++k) {
+        const int dy = k % 3 - 1, dz = k / 3 - 1;
+        const int yy = y + dy < 0 ? geo.ny - 1 : (y + dy >= geo.ny ? 0 : y + dy);
+        int zz = z + dz;
+        if (geo.walls)
+          zz = (zz < 0 || zz >= geo.nz) ? z : zz;
+        else
+          zz = zz < 0 ? geo.nz - 1 : (zz >= geo.nz ? 0 : zz);
+        const size_t row0 = (static_cast<size_t>(zz) * geo.ny + yy) * nx;
+        const int off = (r * 9 + k) * stride + 4;
+        bulk_row(smem_addr(&st[0][off]), phi + row0, row_bytes, bar);
+        bulk_row(smem_addr(&st[1][off]), mu + row0, row_bytes, bar);
+      }
+    }
+  }
+  // the populations of the two cells, loaded while the copies fly
+  const int idx = b0 + (threadIdx.x >> 5) * (2 * kTile) + (threadIdx.x & 31);
+  const bool active = idx < geo.n;
+  int x = 0, y = 0, z = 0;
+  if (active) cell_coords(geo, idx, x, y, z);
+  const Nbr na = make_nbr(geo, x, y, z), nb2 = make_nbr(geo, x + kTile, y, z);
+  float ga[15], fa[7], pa[3], gb[15], fb[7], pb[3];
+  if (active) {
+    load_cell<kAB, S, true>(src, geo, idx, na, ga, fa, pa);
+    load_cell<kAB, S, true>(src, geo, idx + kTile, nb2, gb, fb, pb);
+  }
+  __syncthreads();  // the barrier is initialised and armed before anyone polls it
+  if (!__syncthreads_and(mbar_wait(bar, 0, polls))) {
+    if (threadIdx.x == 0) atomicMax(err, mbar_wait(bar, 0, kMbarSpins) ? 1 : 2);
+    __syncthreads();
+    return;
+  }
+  // periodic x halo of every row copy: column -1 = nx - 1, column nx = 0
+  for (int k = threadIdx.x; k < 2 * 9 * rows * 2; k += blockDim.x) {
+    const int side = k & 1, rk = (k >> 1) % (9 * rows), f = (k >> 1) / (9 * rows);
+    float* row = &st[f][rk * stride + 4];
+    if (side)
+      row[nx] = row[0];
+    else
+      row[-1] = row[nx - 1];
+  }
+  __syncthreads();
+  if (!active) return;
+  // stencil of the cell at x in block row r from the staged rows (k = 3 (dz + 1) + dy + 1)
+  const int r = (idx - b0) / nx;
+  auto stencil = [&](const float* a, int xc) {
+    const float* base = a + r * 9 * stride + 4 + xc;
+    auto row = [&](int dy, int dz) { return base + (3 * (dz + 1) + dy + 1) * stride; };
+    Stencil s;
+    s.c = row(0, 0)[0];
+    s.xm = row(0, 0)[-1];
+    s.xp = row(0, 0)[1];
+    s.ym = row(-1, 0)[0];
+    s.yp = row(1, 0)[0];
+    s.zm = row(0, -1)[0];
+    s.zp = row(0, 1)[0];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      s.k[b] = row((b & 2) ? 1 : -1, (b & 4) ? 1 : -1)[(b & 1) ? 1 : -1];
+    return s;
+  };
+  StencilV<float2> sp, sm;
+  {
+    const Stencil s0 = stencil(st[0], x), s1 = stencil(st[0], x + kTile);
+    sp.c = make_float2(s0.c, s1.c);
+    sp.xm = make_float2(s0.xm, s1.xm);
+    sp.xp = make_float2(s0.xp, s1.xp);
+    sp.ym = make_float2(s0.ym, s1.ym);
+    sp.yp = make_float2(s0.yp, s1.yp);
+    sp.zm = make_float2(s0.zm, s1.zm);
+    sp.zp = make_float2(s0.zp, s1.zp);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) sp.k[b] = make_float2(s0.k[b], s1.k[b]);
+  }
+  {
+    const Stencil s0 = stencil(st[1], x), s1 = stencil(st[1], x + kTile);
+    sm.c = make_float2(s0.c, s1.c);
+    sm.xm = make_float2(s0.xm, s1.xm);
+    sm.xp = make_float2(s0.xp, s1.xp);
+    sm.ym = make_float2(s0.ym, s1.ym);
+    sm.yp = make_float2(s0.yp, s1.yp);
+    sm.zm = make_float2(s0.zm, s1.zm);
+    sm.zp = make_float2(s0.zp, s1.zp);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) sm.k[b] = make_float2(s0.k[b], s1.k[b]);
+  }
+  float2 g[15], f[7], prev[3], cur[3];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) g[i] = make_float2(ga[i], gb[i]);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i] = make_float2(fa[i], fb[i]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) prev[a] = make_float2(pa[a], pb[a]);
+  pair_compute<VAR, S>(ph, have_prev, g, f, prev, sp, sm, cur);
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    ga[i] = g[i].x;
+    gb[i] = g[i].y;
+  }
+  store_g<kAB, S>(dst, idx, na, ga);
+  store_g<kAB, S>(dst, idx + kTile, nb2, gb);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    dst[phiu_index<S>(idx, a)] = cur[a].x;
+    dst[phiu_index<S>(idx + kTile, a)] = cur[a].y;
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    fa[i] = f[i].x;
+    fb[i] = f[i].y;
+  }
+  store_f<kAB, S>(dst, idx, na, fa);
+  store_f<kAB, S>(dst, idx + kTile, nb2, fb);
+}
+
 // Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
 // each warp leaves 5 doubles in parts[5 w ..] (w = its first cell / 32; warp_sums_store).
 // The 32 cells of a warp are summed in FP32 by a fixed butterfly (FP64 throughput on
@@ -687,12 +847,15 @@ cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Ph
 
 template <int VAR>
 void collide_variant(const float* src, float* dst, const float* phi, const float* mu,
-                     const Geometry& geo, const Physics& ph, int pattern, int prev,
-                     cudaStream_t st) {
+                     const Geometry& geo, const Physics& ph, int pattern, int prev, int* err,
+                     long long polls, cudaStream_t st) {
   const unsigned blocks = blocks_for(geo.n);
 #define LBM_COLLIDE_P(S)                                                                    \
   {                                                                                         \
-    if (pattern == kAB && geo.pairs)                                                        \
+    if (pattern == kAB && geo.pairs && geo.stage && err)                                    \
+      k_collide2t<VAR, S><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev,     \
+                                                        err, polls);                       \
+    else if (pattern == kAB && geo.pairs)                                                   \
       k_collide2<VAR, S, false><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,     \
                                                                prev, nullptr);              \
     else if (pattern == kAB)                                                                \
@@ -713,17 +876,26 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
 
 cudaError_t launch_collide(const float* src, float* dst, const float* phi, const float* mu,
                            const Geometry& geo, const Physics& ph, int pattern, bool have_prev,
-                           cudaStream_t st) {
+                           cudaStream_t st, int* err, long long polls) {
   const int prev = have_prev ? 1 : 0;
   const int var = (ph.srt_flow ? kVarSrtFlow : 0) | (ph.d3q7_stencil ? kVarD3Q7 : 0);
   switch (var) {
-    case 0: collide_variant<0>(src, dst, phi, mu, geo, ph, pattern, prev, st); break;
-    case kVarSrtFlow: collide_variant<kVarSrtFlow>(src, dst, phi, mu, geo, ph, pattern, prev, st); break;
-    case kVarD3Q7: collide_variant<kVarD3Q7>(src, dst, phi, mu, geo, ph, pattern, prev, st); break;
+    case 0: collide_variant<0>(src, dst, phi, mu, geo, ph, pattern, prev, err, polls, st); break;
+    case kVarSrtFlow:
+      collide_variant<kVarSrtFlow>(src, dst, phi, mu, geo, ph, pattern, prev, err, polls, st);
+      break;
+    case kVarD3Q7:
+      collide_variant<kVarD3Q7>(src, dst, phi, mu, geo, ph, pattern, prev, err, polls, st);
+      break;
     default:
-      collide_variant<kVarSrtFlow | kVarD3Q7>(src, dst, phi, mu, geo, ph, pattern, prev, st);
+      collide_variant<kVarSrtFlow | kVarD3Q7>(src, dst, phi, mu, geo, ph, pattern, prev, err,
+                                              polls, st);
   }
   return cudaGetLastError();
+}
+
+bool stage_shape_ok(const Geometry& geo) {
+  return geo.nx == 64 || geo.nx == 128 || geo.nx == 256;
 }
 
 int cell_warps(long long n) { return static_cast<int>((n + 31) / 32); }

@@ -81,3 +81,51 @@ def test_pairs_only_where_they_apply(L):
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 0
         with pytest.raises(L.LbmError):
             L.lbm_set_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS, 2)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("case", ["walls", "periodic"])
+def test_staged_stencils_equal_loaded_stencils(L, storage, case):
+    """LBM_TUNE_STENCIL_STAGE: the two-cell pass fetching its blocks' phi and mu rows
+    into shared memory by TMA bulk copies reads the same values as the per-cell stencil
+    loads (nx = 64 walled, 128 periodic: 4 and 2 rows per block)."""
+    w = _workload(case, seed=24)
+    st = L.STORAGES[storage]
+    with L.Solver(w, storage=st) as a, L.Solver(w, storage=st) as b, L.Solver(w, storage=st) as c:
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_STENCIL_STAGE) == 1
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_STENCIL_STAGE, 0)
+        assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0
+        L.lbm_set_tuning(c.ctx, L.LBM_TUNE_CELL_PAIRS, 0)
+        assert L.lbm_get_tuning(c.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0
+        for n in (1, 2, 4):
+            for s in (a, b, c):
+                s.step(n)
+            _same(a, b)
+            _same(a, c)
+
+
+def test_staged_stencils_for_the_variants_and_grid_shapes(L):
+    for variant in ("srt_flow", "d3q7_stencil"):
+        w = _workload("walls", seed=25)
+        setattr(w, variant if variant == "srt_flow" else "stencil",
+                True if variant == "srt_flow" else "d3q7")
+        with L.Solver(w) as a, L.Solver(w) as b:
+            L.lbm_set_tuning(b.ctx, L.LBM_TUNE_STENCIL_STAGE, 0)
+            a.step(3)
+            b.step(3)
+            _same(a, b)
+    # a block's 256 cells straddle two planes (64 x 10 planes of 640 cells) and the last
+    # block is half full (n = 64 x 10 x 3 = 1920 = 7.5 blocks)
+    w = I.perturbed(I.droplet(n=64, R=4.0, nx=64, ny=10, nz=3), seed=26, phi_amp=0.02,
+                    u_amp=0.01, p_amp=1e-3)
+    with L.Solver(w) as a, L.Solver(w) as b:
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_STENCIL_STAGE) == 1
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_CELL_PAIRS, 0)
+        a.step(3)
+        b.step(3)
+        _same(a, b)
+    # nx = 192: pairs, but rows of 192 cells do not tile a block of 256: no staging
+    w = I.droplet(n=32, R=6.0, nx=192, ny=4, nz=4)
+    with L.Solver(w) as s:
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 1
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0
