@@ -254,8 +254,9 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * LBM_PATTERN_AB take two cells per thread (cells x and x + 32 of a row, nx a multiple
  * of 64), doing the arithmetic of both in paired FP32 instructions; lbm_get_tuning
  * reports 1 only while it applies.  Identical results.
- * LBM_TUNE_STENCIL_STAGE: 1 (default) lets that two-cell pass, on grids whose rows are
- * 64, 128 or 256 cells, fetch the rows of phi and mu its block's stencils need into
+ * LBM_TUNE_STENCIL_STAGE: 1 (default with FP32 populations; 0 with 16-bit ones, where it
+ * is slower) lets that two-cell pass, on grids whose rows are 64, 128 or 256 cells,
+ * fetch the rows of phi and mu its block's stencils need into
  * shared memory with TMA bulk copies (one per row and field) instead of loading each
  * stencil value per cell; its wait for the copies is bounded like the chemical-potential
  * pass's (LBM_TUNE_TMA_WAIT_POLLS, same error reporting).  lbm_get_tuning reports 1 only

@@ -92,6 +92,9 @@ def test_staged_stencils_equal_loaded_stencils(L, storage, case):
     w = _workload(case, seed=24)
     st = L.STORAGES[storage]
     with L.Solver(w, storage=st) as a, L.Solver(w, storage=st) as b, L.Solver(w, storage=st) as c:
+        # on by default with FP32 populations only
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_STENCIL_STAGE) == (storage == "fp32")
+        L.lbm_set_tuning(a.ctx, L.LBM_TUNE_STENCIL_STAGE, 1)
         assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_STENCIL_STAGE) == 1
         L.lbm_set_tuning(b.ctx, L.LBM_TUNE_STENCIL_STAGE, 0)
         assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0
