@@ -434,7 +434,10 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
     LBM_CK(c, timed(c, 2, [&] {
              return sums_out ? lbm::launch_collide_sums(src, dst, c->phi, c->mu, c->geo, c->ph,
                                                          pat, prev, c->step_parts, c->partial,
-                                                         sums_out, c->stream)
+                                                         sums_out, c->stream, error_word(c),
+                                                         c->tma_polls < 0
+                                                             ? lbm::mu_tma_default_polls()
+                                                             : c->tma_polls)
                              : lbm::launch_collide(src, dst, c->phi, c->mu, c->geo, c->ph, pat,
                                                    prev, c->stream, error_word(c),
                                                    c->tma_polls < 0 ? lbm::mu_tma_default_polls()

@@ -74,7 +74,7 @@ int cell_warps(long long n);
 cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
                                 const Geometry& geo, const Physics& ph, int pattern,
                                 bool have_prev, double* parts, double* partial, double* out,
-                                cudaStream_t st);
+                                cudaStream_t st, int* err = nullptr, long long polls = 0);
 
 // The fixed-order FP64 reduction of the per-warp partials of the step sums (the tail of
 // launch_collide_sums): parts -> partial -> out (5 doubles).

@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
 // from shared memory: no stencil load instructions and no stencil registers in flight.
 // The values are those load_stencil reads, so the state is bit-identical to k_collide2.
 // A block whose wait runs out waits once more (bounded), sets *err as k_mu_tma does,
-// and returns without touching the state.
+// and returns without touching the state.  With SUMS each warp leaves the sums of its
+// two tiles in parts, as k_collide2.
 constexpr int kStRowPad = 8;                            // floats: 4 before, 4 after a row
 constexpr int kStFloats = 9 * 4 * (64 + kStRowPad);    // per field, max over nx = 64..256
 
@@ -320,11 +321,11 @@ __device__ __forceinline__ void bulk_row(unsigned dst, const float* src, unsigne
       : "memory");
 }
 
-template <int VAR, int S>
+template <int VAR, int S, bool SUMS>
 __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
     k_collide2t(const float* src, float* dst, const float* __restrict__ phi,
                 const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev, int* err,
-                long long polls) {
+                long long polls, double* __restrict__ parts) {
   __shared__ alignas(128) float st[2][kStFloats];
   __shared__ alignas(8) unsigned long long bar_storage;
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
@@ -384,6 +385,8 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
       row[-1] = row[nx - 1];
   }
   __syncthreads();
+  // with SUMS every lane of a warp takes part in the warp sums; a warp is wholly inside
+  // or outside the grid (n is a multiple of 64)
   if (!active) return;
   // stencil of the cell at x in block row r from the staged rows (k = 3 (dz + 1) + dy + 1)
   const int r = (idx - b0) / nx;
@@ -436,6 +439,15 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
 #pragma unroll
   for (int a = 0; a < 3; ++a) prev[a] = make_float2(pa[a], pb[a]);
   pair_compute<VAR, S>(ph, have_prev, g, f, prev, sp, sm, cur);
+  if (SUMS) {
+    float s4[8];
+    pair_sums<S>(g, f, sp.c, na, 0, s4);
+    pair_sums<S>(g, f, sp.c, nb2, 1, s4 + 4);
+    const bool bad0 = !(isfinite(s4[0]) && isfinite(s4[1]) && isfinite(s4[2]) && isfinite(s4[3]));
+    const bool bad1 = !(isfinite(s4[4]) && isfinite(s4[5]) && isfinite(s4[6]) && isfinite(s4[7]));
+    warp_sums_store(s4, bad0, parts, idx & ~31);
+    warp_sums_store(s4 + 4, bad1, parts, (idx + kTile) & ~31);
+  }
 #pragma unroll
   for (int i = 0; i < 15; ++i) {
     ga[i] = g[i].x;
@@ -853,8 +865,8 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
 #define LBM_COLLIDE_P(S)                                                                    \
   {                                                                                         \
     if (pattern == kAB && geo.pairs && geo.stage && err)                                    \
-      k_collide2t<VAR, S><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev,     \
-                                                        err, polls);                       \
+      k_collide2t<VAR, S, false><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,   \
+                                                               prev, err, polls, nullptr);  \
     else if (pattern == kAB && geo.pairs)                                                   \
       k_collide2<VAR, S, false><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,     \
                                                                prev, nullptr);              \
@@ -903,9 +915,17 @@ int cell_warps(long long n) { return static_cast<int>((n + 31) / 32); }
 cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
                                 const Geometry& geo, const Physics& ph, int pattern,
                                 bool have_prev, double* parts, double* partial, double* out,
-                                cudaStream_t st) {
+                                cudaStream_t st, int* err, long long polls) {
   const int prev = have_prev ? 1 : 0;
-  if (pattern == kAB && geo.pairs) {
+  if (pattern == kAB && geo.pairs && geo.stage && err) {
+    const unsigned blocks = blocks_for(geo.n);
+    if (geo.storage == kF16)
+      k_collide2t<0, kF16, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, err, polls, parts);
+    else if (geo.storage == kBF16)
+      k_collide2t<0, kBF16, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, err, polls, parts);
+    else
+      k_collide2t<0, kF32, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, err, polls, parts);
+  } else if (pattern == kAB && geo.pairs) {
     const unsigned blocks = blocks_for(geo.n);
     if (geo.storage == kF16)
       k_collide2<0, kF16, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
