@@ -74,8 +74,11 @@ NCU_TRAFFIC = {
     "k_collide2t": {"bytes_per_cell": 208.41, "kernel_sha": "40d8d69168256c13"},
     # 536.9 MB + 433.2 MB
     "k_collide2_fp16": {"bytes_per_cell": 115.65, "kernel_sha": "40d8d69168256c13"},
-    # 1434.3 MB + 799.7 MB
-    "k_fused": {"bytes_per_cell": 266.32, "kernel_sha": "40d8d69168256c13"},
+    # 856.9 MB + 794.3 MB with segments of 64 planes and no L2 prefetch (the traffic of
+    # the single pass depends on both: 266.3 B per cell with 18 planes and 2 planes of
+    # prefetch)
+    "k_fused": {"bytes_per_cell": 196.84, "kernel_sha": "40d8d69168256c13", "segment": 64,
+                "prefetch": 0},
 }
 
 WORKLOADS = {
@@ -402,6 +405,10 @@ def run_ours(args):
     single_pass = bool(getattr(args, "single_pass", False))
     if single_pass:
         L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED, 1)
+        if getattr(args, "fused_segment", None) is not None:
+            L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED_SEGMENT, args.fused_segment)
+        if getattr(args, "fused_prefetch", None) is not None:
+            L.lbm_set_tuning(ctx, L.LBM_TUNE_FUSED_PREFETCH, args.fused_prefetch)
 
     group = RankGroup(world, rank, "nccl")
 
@@ -458,6 +465,11 @@ def run_ours(args):
     achieved = coll_bytes * cells / (coll_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
     tr = NCU_TRAFFIC.get(coll_name if wide else f"{coll_name}_{args.storage}")
+    if tr and coll_name == "k_fused":  # the single pass's traffic depends on its settings
+        if (tr.get("segment"), tr.get("prefetch")) != (
+                L.lbm_get_tuning(ctx, L.LBM_TUNE_FUSED_SEGMENT),
+                L.lbm_get_tuning(ctx, L.LBM_TUNE_FUSED_PREFETCH)):
+            tr = None
     traffic = round(tr["bytes_per_cell"] * cells) if tr and tr.get("kernel_sha") == src_hash else None
 
     # ---- end-to-end region through the C ABI with host buffers ---------------
@@ -624,6 +636,10 @@ def main(argv=None):
                     help="population storage of the main run (arithmetic is FP32 in all)")
     ap.add_argument("--single-pass", action="store_true",
                     help="run the main leg with the one-kernel step (LBM_TUNE_FUSED)")
+    ap.add_argument("--fused-segment", type=int, default=None,
+                    help="with --single-pass: planes per block segment (0: by grid size)")
+    ap.add_argument("--fused-prefetch", type=int, default=None,
+                    help="with --single-pass: L2 prefetch distance in planes")
     ap.add_argument("--cell-pairs", type=int, choices=(0, 1), default=1,
                     help="two cells per thread in the stream-collide pass where it applies")
     ap.add_argument("--no-e2e", action="store_true")

@@ -58,7 +58,7 @@ struct lbm_ctx {
   // prefetch distance in planes
   bool use_fused = false;
   int fused_seg = 0;
-  int fused_pf = 2;
+  int fused_pf = 0;
   int sms = 0;
 
   // CUDA graphs of two consecutive steps, one per parity of the stored state (which
