@@ -18,6 +18,10 @@ Printed JSON line (rank 0):
              CUDA-event duration, against the measured HBM copy bandwidth.
   cpu_baseline  the FP64 oracle on a bounded sample, one single-threaded replica per host
              core (rank 0, N = 1).
+  storage_variants / pattern_variants / model_variants  the same measurement with FP16
+             and BF16 storage, the in-place pattern, the single-pass step, the SRT flow
+             lattice, the D3Q7-weighted stencils, and interface tracking with the
+             prescribed deformation field (periodic 256^3).
   serving    the request loop: a seeded Poisson stream of Rayleigh-Taylor runs of
              mixed grids served by continuous batching and one at a time; p50/p99
              time to solution and aggregate MLUPS of each (step counts scaled by
@@ -29,6 +33,7 @@ the data path).
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import os
@@ -56,6 +61,12 @@ STEP_BYTES_PER_CELL = COLLIDE_BYTES_PER_CELL + (7 + 1) * 4 + (1 + 1) * 4  # + k_
 # plus phi and mu (k_collide); 7 x 2 B of f, the previous phi and the new phi (k_phi).
 COLLIDE_BYTES_PER_CELL_16 = 2 * (22 * 2 + 12) + 8
 STEP_BYTES_PER_CELL_16 = COLLIDE_BYTES_PER_CELL_16 + (7 * 2 + 4 + 4) + 8
+
+# Interface tracking with a prescribed velocity (k_che): read f, phi and mu at the cell
+# and phi u of the previous step (48 B), write f and phi u (40 B); the step adds k_phi
+# and k_mu.
+CHE_BYTES_PER_CELL = (7 + 1 + 1 + 3) * 4 + (7 + 3) * 4
+CHE_STEP_BYTES_PER_CELL = CHE_BYTES_PER_CELL + (7 + 1) * 4 + (1 + 1) * 4
 
 # The one-kernel step (k_fused): the state read and written once (200 B in FP32); with
 # 16-bit populations 2 x (44 + 12) plus phi of the previous step read and the new phi
@@ -524,6 +535,7 @@ def run_ours(args):
     # ---- reduced-precision storage variants (same workload and step count) ------
     variants = None
     pattern_variants = None
+    model_variants = None
     if not args.no_variants and args.storage == "fp32":
         solver.close()
         variants = {}
@@ -582,6 +594,51 @@ def run_ours(args):
                 variants[name] = entry
             vs.close()
 
+        # ---- model variants: the SRT flow lattice and the D3Q7-weighted stencils on the
+        # same workload, and interface tracking with the prescribed deformation field of
+        # Eq. 41 on a periodic 256^3 box (the paper's Sec. III B test at twice the size)
+        if args.pattern == "ab":
+            model_variants = {}
+            srt = copy.copy(w)
+            srt.srt_flow = True
+            d7 = copy.copy(w)
+            d7.stencil = "d3q7"
+            mruns = [("srt_flow", srt, "k_collide", COLLIDE_BYTES_PER_CELL, STEP_BYTES_PER_CELL),
+                     ("d3q7_stencil", d7, "k_collide", COLLIDE_BYTES_PER_CELL,
+                      STEP_BYTES_PER_CELL),
+                     ("interface_tracking", I.deformation(n=256), "k_che", CHE_BYTES_PER_CELL,
+                      CHE_STEP_BYTES_PER_CELL)]
+            for name, wv, kname, cb, sb in mruns:
+                vs = L.Solver(wv, stream=stream.cuda_stream)
+                vs.step(args.warmup)
+                vt = tune.autotune(vs.ctx) if not args.no_tune else None
+                L.lbm_profile(vs.ctx, True)
+                barrier()
+                v0 = torch.cuda.Event(enable_timing=True)
+                v1 = torch.cuda.Event(enable_timing=True)
+                v0.record(stream)
+                vs.step(args.steps)
+                v1.record(stream)
+                barrier()
+                vms = max_over_ranks(v0.elapsed_time(v1))
+                cms, cn = L.lbm_profile_read(vs.ctx, L.KERNEL_COLLIDE)
+                cmean = cms / max(cn, 1)
+                entry = {
+                    "workload": wv.name if name == "interface_tracking" else "as the main line",
+                    "cells": wv.cells,
+                    "value": round(aggregate_mlups(wv.cells, args.steps, world, vms * 1e-3), 3),
+                    "unit": UNIT, "ms_per_step": round(vms / args.steps, 5),
+                    "kernel": kname, "kernel_ms": round(cmean, 5),
+                    "kernel_bytes_per_cell": cb,
+                    "kernel_frac": round(cb * wv.cells / (cmean * 1e-3) / 1e9 / peak, 4),
+                    "step_bytes_per_cell": sb,
+                    "step_hbm_frac": round(sb * wv.cells * args.steps / (vms * 1e-3) / 1e9 / peak,
+                                           4)}
+                if vt:
+                    entry["tuning"] = {k: v["value"] for k, v in vt.items()}
+                model_variants[name] = entry
+                vs.close()
+
     if variants is None:
         solver.close()
 
@@ -613,6 +670,7 @@ def run_ours(args):
                 "kernels": kernels,
                 "tuning": {k: v["value"] for k, v in tuning.items()} if tuning else None,
                 "storage_variants": variants, "pattern_variants": pattern_variants,
+                "model_variants": model_variants,
                 "serving": serving,
                 "cpu_baseline": cpu, "e2e": e2e, "e2e_sustained": e2e_sustained, "clocks": clock,
                 "gpu_launches": (1 if coll_name == "k_fused" else 3) * args.steps,
