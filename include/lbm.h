@@ -250,8 +250,8 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * default, chooses by grid size; each segment also forms phi on 2 planes and mu on 1
  * plane beyond each of its ends).  LBM_TUNE_FUSED_PREFETCH: how many planes ahead each
  * block prefetches its tiles into L2 (default 0, off; at most 64).
- * LBM_TUNE_CELL_PAIRS: 1 (default) lets the three-kernel step's stream-collide pass of
- * LBM_PATTERN_AB take two cells per thread (cells x and x + 32 of a row, nx a multiple
+ * LBM_TUNE_CELL_PAIRS: 1 (default) lets the three-kernel step's stream-collide pass
+ * (either pattern) take two cells per thread (cells x and x + 32 of a row, nx a multiple
  * of 64), doing the arithmetic of both in paired FP32 instructions; lbm_get_tuning
  * reports 1 only while it applies.  Identical results.
  * LBM_TUNE_STENCIL_STAGE: 1 (default with FP32 populations; 0 with 16-bit ones, where it

@@ -552,10 +552,11 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
           (1LL << 31))
     c->row_tiles = grid->nx / lbm::kTile;
   c->geo.row_tiles = c->row_tiles;
-  // two cells per thread in the two-array stream-collide: cells x and x + 32 of one row
-  if (params->pattern == LBM_PATTERN_AB && grid->nx % (2 * lbm::kTile) == 0) c->pairs = 1;
+  // two cells per thread in the stream-collide (either pattern): cells x and x + 32 of a row
+  if (grid->nx % (2 * lbm::kTile) == 0) c->pairs = 1;
   c->geo.pairs = c->pairs;
-  if (c->pairs && lbm::stage_shape_ok(c->geo)) c->stage_rows = 1;
+  if (c->pairs && params->pattern == LBM_PATTERN_AB && lbm::stage_shape_ok(c->geo))
+    c->stage_rows = 1;
   // on by default with FP32 populations only: with 16-bit ones the pass is faster
   // loading its stencils per cell (the block waits for all its rows before computing)
   c->geo.stage = params->storage == LBM_STORAGE_FP32 ? c->stage_rows : 0;

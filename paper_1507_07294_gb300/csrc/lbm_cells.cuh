@@ -497,10 +497,11 @@ __device__ __forceinline__ void pair_sums(const float2 g[15], const float2 f[7],
 }
 
 // The stream-collide body for cells idx and idx + kTile (the same lane of two adjacent
-// tiles of one row; pattern AB): loads and stores per cell, the arithmetic once for both
-// (pair_compute).  With SUMS, sums[0..3] and sums[4..7] receive the two cells'
-// contributions (as collide_loaded).
-template <int VAR, int S, bool SUMS>
+// tiles of one row) with pattern P: loads and stores per cell, the arithmetic once for
+// both (pair_compute).  Both cells are loaded before either is stored, so the in-place
+// patterns (src == dst) stay race-free as in collide_cell.  With SUMS, sums[0..3] and
+// sums[4..7] receive the two cells' contributions (as collide_loaded).
+template <int VAR, int S, bool SUMS, int P = kAB>
 __device__ __forceinline__ void collide_pair(const float* src, float* dst,
                                              const float* __restrict__ phi,
                                              const float* __restrict__ mu, const Geometry& geo,
@@ -511,8 +512,8 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
   const int idx2 = idx + kTile;
   const Nbr na = make_nbr(geo, x, y, z), nb2 = make_nbr(geo, x + kTile, y, z);
   float ga[15], fa[7], pa[3], gb[15], fb[7], pb[3];
-  load_cell<kAB, S, true>(src, geo, idx, na, ga, fa, pa);
-  load_cell<kAB, S, true>(src, geo, idx2, nb2, gb, fb, pb);
+  load_cell<P, S, true>(src, geo, idx, na, ga, fa, pa);
+  load_cell<P, S, true>(src, geo, idx2, nb2, gb, fb, pb);
   const StencilV<float2> sp = pair_stencil(phi, idx, na, idx2, nb2);
   const StencilV<float2> sm = pair_stencil(mu, idx, na, idx2, nb2);
   float2 g[15], f[7], prev[3], cur[3];
@@ -532,8 +533,22 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
     ga[i] = g[i].x;
     gb[i] = g[i].y;
   }
-  store_g<kAB, S>(dst, idx, na, ga);
-  store_g<kAB, S>(dst, idx2, nb2, gb);
+  // the odd in-place step stores to the neighbours' slots: by rows off the walls, as
+  // collide_loaded does
+  auto put_g = [&](int i, const Nbr& nb, const float* v) {
+    if (P == kAAOdd && use_rows<P>(geo, nb))
+      row_store_g_odd<S>(row_pull<S>(dst, nb, i), v);
+    else
+      store_g<P, S>(dst, i, nb, v);
+  };
+  auto put_f = [&](int i, const Nbr& nb, const float* v) {
+    if (P == kAAOdd && use_rows<P>(geo, nb))
+      row_store_f_odd<S>(row_pull<S>(dst, nb, i), v);
+    else
+      store_f<P, S>(dst, i, nb, v);
+  };
+  put_g(idx, na, ga);
+  put_g(idx2, nb2, gb);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     dst[phiu_index<S>(idx, a)] = cur[a].x;
@@ -544,8 +559,8 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
     fa[i] = f[i].x;
     fb[i] = f[i].y;
   }
-  store_f<kAB, S>(dst, idx, na, fa);
-  store_f<kAB, S>(dst, idx2, nb2, fb);
+  put_f(idx, na, fa);
+  put_f(idx2, nb2, fb);
 }
 
 // Sums of the fused step sums over the 32 cells of a warp, stored as 5 doubles at

@@ -36,8 +36,8 @@ struct Geometry {
   int storage;           // population storage type (Storage); selects the kernel instance
   int row_tiles;         // nx / kTile when rows are whole tiles and a plane of tiles spans
                          // < 2^31 bytes (pull addressing of RowPull), else 0
-  int pairs;             // 1: the two-array stream-collide takes two cells per thread
-                         // (k_collide2; needs row_tiles and nx a multiple of 2 kTile)
+  int pairs;             // 1: the stream-collide takes two cells per thread (k_collide2,
+                         // either pattern; needs nx a multiple of 2 kTile)
   int stage;             // 1: k_collide2 stages the phi and mu stencils in shared memory
                          // by TMA bulk copies (k_collide2t; needs pairs and nx of 64,
                          // 128 or 256)

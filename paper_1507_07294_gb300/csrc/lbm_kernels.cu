@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
 // k_collide with two cells per thread (collide_pair, the arithmetic in paired FP32
 // instructions): block b takes cells 256 b .. 256 b + 255 as 4 pairs of adjacent tiles of
 // one row; lane l of warp w the cells 256 b + 64 w + l and 256 b + 64 w + 32 + l.  Pattern
-// AB on grids with Geometry::pairs (n is then a multiple of 64, so a warp is wholly
-// inside or outside the grid).  With SUMS each warp leaves the sums of its two tiles in
-// parts, as k_collide_sums.
+// P (two arrays, or either step of the in-place pattern) on grids with Geometry::pairs (n
+// is then a multiple of 64, so a warp is wholly inside or outside the grid).  With SUMS
+// each warp leaves the sums of its two tiles in parts, as k_collide_sums.
 // 4 resident blocks of 128 threads (128 registers, no spills); at 5 the 16-bit kernels
 // spill and run 17 % slower.
 template <int S>
@@ -277,7 +277,7 @@ constexpr int collide2_min_blocks() {
   return 4;
 }
 
-template <int VAR, int S, bool SUMS>
+template <int VAR, int S, bool SUMS, int P = kAB>
 __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
     k_collide2(const float* src, float* dst, const float* __restrict__ phi,
                const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev,
@@ -287,13 +287,13 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
   if (idx >= geo.n) return;
   if (SUMS) {
     float s[8];
-    collide_pair<VAR, S, true>(src, dst, phi, mu, geo, ph, have_prev, idx, s);
+    collide_pair<VAR, S, true, P>(src, dst, phi, mu, geo, ph, have_prev, idx, s);
     const bool bad0 = !(isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]) && isfinite(s[3]));
     const bool bad1 = !(isfinite(s[4]) && isfinite(s[5]) && isfinite(s[6]) && isfinite(s[7]));
     warp_sums_store(s, bad0, parts, idx & ~31);
     warp_sums_store(s + 4, bad1, parts, (idx + kTile) & ~31);
   } else {
-    collide_pair<VAR, S, false>(src, dst, phi, mu, geo, ph, have_prev, idx, nullptr);
+    collide_pair<VAR, S, false, P>(src, dst, phi, mu, geo, ph, have_prev, idx, nullptr);
   }
 }
 
@@ -872,6 +872,12 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
                                                                prev, nullptr);              \
     else if (pattern == kAB)                                                                \
       k_collide<kAB, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev);     \
+    else if (pattern == kAAEven && geo.pairs)                                               \
+      k_collide2<VAR, S, false, kAAEven><<<blocks, kBlock / 2, 0, st>>>(                    \
+          src, dst, phi, mu, geo, ph, prev, nullptr);                                       \
+    else if (pattern == kAAOdd && geo.pairs)                                                \
+      k_collide2<VAR, S, false, kAAOdd><<<blocks, kBlock / 2, 0, st>>>(                     \
+          src, dst, phi, mu, geo, ph, prev, nullptr);                                       \
     else if (pattern == kAAEven)                                                            \
       k_collide<kAAEven, VAR, S><<<blocks, kBlock, 0, st>>>(src, dst, phi, mu, geo, ph, prev); \
     else                                                                                    \
@@ -933,6 +939,23 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
       k_collide2<0, kBF16, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
     else
       k_collide2<0, kF32, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
+  } else if ((pattern == kAAEven || pattern == kAAOdd) && geo.pairs) {
+    const unsigned blocks = blocks_for(geo.n);
+#define LBM_SUMS_AA(S)                                                                        \
+  if (pattern == kAAEven)                                                                     \
+    k_collide2<0, S, true, kAAEven><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, \
+                                                                   prev, parts);              \
+  else                                                                                        \
+    k_collide2<0, S, true, kAAOdd><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,  \
+                                                                  prev, parts);
+    if (geo.storage == kF16) {
+      LBM_SUMS_AA(kF16)
+    } else if (geo.storage == kBF16) {
+      LBM_SUMS_AA(kBF16)
+    } else {
+      LBM_SUMS_AA(kF32)
+    }
+#undef LBM_SUMS_AA
   } else {
     LBM_DISPATCH(geo, pattern, k_collide_sums, src, dst, phi, mu, geo, ph, prev, parts);
   }

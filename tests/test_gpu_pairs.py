@@ -78,7 +78,8 @@ def test_pairs_only_where_they_apply(L):
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 0
     w = _workload("walls", seed=23)
     with L.Solver(w, pattern=L.LBM_PATTERN_AA) as s:
-        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 0
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 1
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0  # two-array only
         with pytest.raises(L.LbmError):
             L.lbm_set_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS, 2)
 
@@ -132,3 +133,30 @@ def test_staged_stencils_for_the_variants_and_grid_shapes(L):
     with L.Solver(w) as s:
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 1
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("case", ["walls", "periodic"])
+def test_in_place_pattern_pairs(L, storage, case):
+    """The in-place pattern with two cells per thread (both of its steps, in place)
+    equals it with one cell per thread and equals the two-array pattern, across odd and
+    even step counts, graph replays and the fused step sums."""
+    w = _workload(case, seed=28)
+    st = L.STORAGES[storage]
+    with L.Solver(w, storage=st, pattern=L.LBM_PATTERN_AA) as a, \
+            L.Solver(w, storage=st, pattern=L.LBM_PATTERN_AA) as b, \
+            L.Solver(w, storage=st) as c:
+        assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_CELL_PAIRS) == 1
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_CELL_PAIRS, 0)
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_GRAPHS, 0)
+        for n in (1, 2, 3, 4):
+            for s in (a, b, c):
+                s.step(n)
+            _same(a, b)
+            _same(a, c)
+        ra = L.lbm_step_reduce(a.ctx, 3)
+        rb = L.lbm_step_reduce(b.ctx, 3)
+        rc = L.lbm_step_reduce(c.ctx, 3)
+        assert ra[0] == rb[0] == rc[0]
+        assert np.array_equal(ra[1], rb[1]) and np.array_equal(ra[1], rc[1])
+        _same(a, c)
