@@ -568,8 +568,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
       c->geo.prefetch_collide =
           sms * lbm::resident_blocks_per_sm(c->geo.pairs ? 3 : 0, c->geo.storage);
       c->geo.prefetch_phi =
-          sms * lbm::resident_blocks_per_sm(1, c->geo.storage,
-                                            c->geo.row_tiles > 0 && params->pattern == LBM_PATTERN_AB);
+          sms * lbm::resident_blocks_per_sm(1, c->geo.storage, c->geo.row_tiles > 0);
     }
   }
   c->ph = make_physics(*params);

@@ -53,7 +53,9 @@ __global__ void __launch_bounds__(kBlock) k_phi(const float* __restrict__ src,
 }
 
 // ------------------------------------------------------------- k_phi_rows ---------
-// k_phi for pattern AB on grids whose rows are whole tiles (Geometry::row_tiles > 0):
+// k_phi on grids whose rows are whole tiles (Geometry::row_tiles > 0), for the pulls of
+// pattern P (AB: slot i of x - c_i; the even in-place step: slot i of the cell itself;
+// the odd one: slot opp(i) of x - c_i, across a wall slot i of the cell itself):
 // each warp takes one tile (32 cells of a row) through kPhiRowsK consecutive planes, so
 // the neighbour deltas and the coordinate bookkeeping are computed once per column
 // rather than once per cell, and all loads of the column are issued before the first
@@ -80,7 +82,7 @@ __device__ __forceinline__ void prefetch_rows_ahead(const float* src, const Geom
                 bytes);
 }
 
-template <int S>
+template <int S, int P = kAB>
 __global__ void __launch_bounds__(kBlock) k_phi_rows(const float* __restrict__ src,
                                                      const float* phi_ref, float* phi,
                                                      Geometry geo, int ahead) {
@@ -113,18 +115,36 @@ __global__ void __launch_bounds__(kBlock) k_phi_rows(const float* __restrict__ s
     if (k < nk) {
       const int z = z0 + k;
       const char* o = own + k * plane_b;
-      // f_5 comes from z - 1 and f_6 from z + 1; across a wall each is the cell's own
-      // opposite slot (6 and 5), i.e. one slot further and one slot back
-      const char* zm = z > 0 ? o - plane_b : (geo.walls ? o + SL : o + (geo.nz - 1) * plane_b);
-      const char* zp = z < geo.nz - 1 ? o + plane_b
-                                      : (geo.walls ? o - SL : o - (geo.nz - 1) * plane_b);
       f[k][0] = get(o);
-      f[k][1] = get(o + dxm + 1 * SL);
-      f[k][2] = get(o + dxp + 2 * SL);
-      f[k][3] = get(o + dym + 3 * SL);
-      f[k][4] = get(o + dyp + 4 * SL);
-      f[k][5] = get(zm + 5 * SL);
-      f[k][6] = get(zp + 6 * SL);
+      if (P == kAAEven) {
+#pragma unroll
+        for (int i = 1; i < 7; ++i) f[k][i] = get(o + i * SL);
+      } else if (P == kAAOdd) {
+        // slot opp(i) of x - c_i: f_5 from slot 6 of z - 1, f_6 from slot 5 of z + 1;
+        // across a wall each is the cell's own slot (5 and 6), one slot back and one
+        // further
+        const char* zm = z > 0 ? o - plane_b : (geo.walls ? o - SL : o + (geo.nz - 1) * plane_b);
+        const char* zp = z < geo.nz - 1 ? o + plane_b
+                                        : (geo.walls ? o + SL : o - (geo.nz - 1) * plane_b);
+        f[k][1] = get(o + dxm + 2 * SL);
+        f[k][2] = get(o + dxp + 1 * SL);
+        f[k][3] = get(o + dym + 4 * SL);
+        f[k][4] = get(o + dyp + 3 * SL);
+        f[k][5] = get(zm + 6 * SL);
+        f[k][6] = get(zp + 5 * SL);
+      } else {
+        // f_5 comes from z - 1 and f_6 from z + 1; across a wall each is the cell's own
+        // opposite slot (6 and 5), i.e. one slot further and one slot back
+        const char* zm = z > 0 ? o - plane_b : (geo.walls ? o + SL : o + (geo.nz - 1) * plane_b);
+        const char* zp = z < geo.nz - 1 ? o + plane_b
+                                        : (geo.walls ? o - SL : o - (geo.nz - 1) * plane_b);
+        f[k][1] = get(o + dxm + 1 * SL);
+        f[k][2] = get(o + dxp + 2 * SL);
+        f[k][3] = get(o + dym + 3 * SL);
+        f[k][4] = get(o + dyp + 4 * SL);
+        f[k][5] = get(zm + 5 * SL);
+        f[k][6] = get(zp + 6 * SL);
+      }
       if (S != kF32) ref[k] = phi_ref[cell0 + k * geo.plane];
     }
   }
@@ -813,17 +833,26 @@ cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const
                        int pattern, cudaStream_t st) {
   const int tp = geo.plane / kTile;
   const int chunks = (geo.nz + kPhiRowsK - 1) / kPhiRowsK;
-  if (pattern == kAB && geo.row_tiles > 0 && chunks <= 65535) {
+  if (geo.row_tiles > 0 && chunks <= 65535) {
     const dim3 grid((tp + kBlock / kTile - 1) / (kBlock / kTile), chunks);
     const int ahead = geo.prefetch_phi > 0
                           ? static_cast<int>((geo.prefetch_phi + grid.x - 1) / grid.x)
                           : 0;
-    if (geo.storage == kF16)
-      k_phi_rows<kF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
-    else if (geo.storage == kBF16)
-      k_phi_rows<kBF16><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
-    else
-      k_phi_rows<kF32><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
+#define LBM_PHI_ROWS(S)                                                                   \
+  if (pattern == kAAEven)                                                                 \
+    k_phi_rows<S, kAAEven><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);       \
+  else if (pattern == kAAOdd)                                                             \
+    k_phi_rows<S, kAAOdd><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);        \
+  else                                                                                    \
+    k_phi_rows<S, kAB><<<grid, kBlock, 0, st>>>(src, phi_ref, phi, geo, ahead);
+    if (geo.storage == kF16) {
+      LBM_PHI_ROWS(kF16)
+    } else if (geo.storage == kBF16) {
+      LBM_PHI_ROWS(kBF16)
+    } else {
+      LBM_PHI_ROWS(kF32)
+    }
+#undef LBM_PHI_ROWS
     return cudaGetLastError();
   }
   LBM_DISPATCH(geo, pattern, k_phi, src, phi_ref, phi, geo);
