@@ -255,12 +255,12 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * of 64), doing the arithmetic of both in paired FP32 instructions; lbm_get_tuning
  * reports 1 only while it applies.  Identical results.
  * LBM_TUNE_STENCIL_STAGE: 1 (default with FP32 populations; 0 with 16-bit ones, where it
- * is slower) lets that two-cell pass, on grids whose rows are 64, 128 or 256 cells,
- * fetch the rows of phi and mu its block's stencils need into
- * shared memory with TMA bulk copies (one per row and field) instead of loading each
- * stencil value per cell; its wait for the copies is bounded like the chemical-potential
- * pass's (LBM_TUNE_TMA_WAIT_POLLS, same error reporting).  lbm_get_tuning reports 1 only
- * while it applies.  Identical results.
+ * is slower) lets that two-cell pass (either pattern), on grids whose rows are 64, 128
+ * or 256 cells, fetch the rows of phi and mu its block's stencils need into shared
+ * memory with TMA bulk copies (one per row and field) instead of loading each stencil
+ * value per cell; its wait for the copies is bounded like the chemical-potential pass's
+ * (LBM_TUNE_TMA_WAIT_POLLS, same error reporting).  lbm_get_tuning reports 1 only while
+ * it applies.  Identical results.
  * Setting any parameter drops the captured graphs (and waits for the context's
  * stream).
  * lbm_set_tuning returns LBM_EINVAL for an unknown parameter or a value out of range. */

@@ -555,8 +555,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   // two cells per thread in the stream-collide (either pattern): cells x and x + 32 of a row
   if (grid->nx % (2 * lbm::kTile) == 0) c->pairs = 1;
   c->geo.pairs = c->pairs;
-  if (c->pairs && params->pattern == LBM_PATTERN_AB && lbm::stage_shape_ok(c->geo))
-    c->stage_rows = 1;
+  if (c->pairs && lbm::stage_shape_ok(c->geo)) c->stage_rows = 1;
   // on by default with FP32 populations only: with 16-bit ones the pass is faster
   // loading its stencils per cell (the block waits for all its rows before computing)
   c->geo.stage = params->storage == LBM_STORAGE_FP32 ? c->stage_rows : 0;

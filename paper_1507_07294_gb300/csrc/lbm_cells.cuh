@@ -496,6 +496,48 @@ __device__ __forceinline__ void pair_sums(const float2 g[15], const float2 f[7],
                   (E::get(E::put(fc[5])) + E::get(E::put(fc[6]))));
 }
 
+// The stores of a pair's post-collision state (cells idx and idx + kTile) with pattern P:
+// g, phi u and f; the odd in-place step writes the neighbours' slots, by rows off the
+// walls, as collide_loaded does.
+template <int P, int S>
+__device__ __forceinline__ void store_pair(float* dst, const Geometry& geo, int idx,
+                                           const Nbr& na, const Nbr& nb2, const float2 g[15],
+                                           const float2 f[7], const float2 cur[3]) {
+  const int idx2 = idx + kTile;
+  auto put_g = [&](int i, const Nbr& nb, const float* v) {
+    if (P == kAAOdd && use_rows<P>(geo, nb))
+      row_store_g_odd<S>(row_pull<S>(dst, nb, i), v);
+    else
+      store_g<P, S>(dst, i, nb, v);
+  };
+  auto put_f = [&](int i, const Nbr& nb, const float* v) {
+    if (P == kAAOdd && use_rows<P>(geo, nb))
+      row_store_f_odd<S>(row_pull<S>(dst, nb, i), v);
+    else
+      store_f<P, S>(dst, i, nb, v);
+  };
+  float a[15], b[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    a[i] = g[i].x;
+    b[i] = g[i].y;
+  }
+  put_g(idx, na, a);
+  put_g(idx2, nb2, b);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dst[phiu_index<S>(idx, k)] = cur[k].x;
+    dst[phiu_index<S>(idx2, k)] = cur[k].y;
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    a[i] = f[i].x;
+    b[i] = f[i].y;
+  }
+  put_f(idx, na, a);
+  put_f(idx2, nb2, b);
+}
+
 // The stream-collide body for cells idx and idx + kTile (the same lane of two adjacent
 // tiles of one row) with pattern P: loads and stores per cell, the arithmetic once for
 // both (pair_compute).  Both cells are loaded before either is stored, so the in-place
@@ -528,39 +570,7 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
     pair_sums<S>(g, f, sp.c, na, 0, sums);
     pair_sums<S>(g, f, sp.c, nb2, 1, sums + 4);
   }
-#pragma unroll
-  for (int i = 0; i < 15; ++i) {
-    ga[i] = g[i].x;
-    gb[i] = g[i].y;
-  }
-  // the odd in-place step stores to the neighbours' slots: by rows off the walls, as
-  // collide_loaded does
-  auto put_g = [&](int i, const Nbr& nb, const float* v) {
-    if (P == kAAOdd && use_rows<P>(geo, nb))
-      row_store_g_odd<S>(row_pull<S>(dst, nb, i), v);
-    else
-      store_g<P, S>(dst, i, nb, v);
-  };
-  auto put_f = [&](int i, const Nbr& nb, const float* v) {
-    if (P == kAAOdd && use_rows<P>(geo, nb))
-      row_store_f_odd<S>(row_pull<S>(dst, nb, i), v);
-    else
-      store_f<P, S>(dst, i, nb, v);
-  };
-  put_g(idx, na, ga);
-  put_g(idx2, nb2, gb);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dst[phiu_index<S>(idx, a)] = cur[a].x;
-    dst[phiu_index<S>(idx2, a)] = cur[a].y;
-  }
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    fa[i] = f[i].x;
-    fb[i] = f[i].y;
-  }
-  put_f(idx, na, fa);
-  put_f(idx2, nb2, fb);
+  store_pair<P, S>(dst, geo, idx, na, nb2, g, f, cur);
 }
 
 // Sums of the fused step sums over the 32 cells of a warp, stored as 5 doubles at

@@ -341,7 +341,7 @@ __device__ __forceinline__ void bulk_row(unsigned dst, const float* src, unsigne
       : "memory");
 }
 
-template <int VAR, int S, bool SUMS>
+template <int VAR, int S, bool SUMS, int P = kAB>
 __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
     k_collide2t(const float* src, float* dst, const float* __restrict__ phi,
                 const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev, int* err,
@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
   const Nbr na = make_nbr(geo, x, y, z), nb2 = make_nbr(geo, x + kTile, y, z);
   float ga[15], fa[7], pa[3], gb[15], fb[7], pb[3];
   if (active) {
-    load_cell<kAB, S, true>(src, geo, idx, na, ga, fa, pa);
-    load_cell<kAB, S, true>(src, geo, idx + kTile, nb2, gb, fb, pb);
+    load_cell<P, S, true>(src, geo, idx, na, ga, fa, pa);
+    load_cell<P, S, true>(src, geo, idx + kTile, nb2, gb, fb, pb);
   }
   __syncthreads();  // the barrier is initialised and armed before anyone polls it
   if (!__syncthreads_and(mbar_wait(bar, 0, polls))) {
@@ -468,25 +468,7 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
     warp_sums_store(s4, bad0, parts, idx & ~31);
     warp_sums_store(s4 + 4, bad1, parts, (idx + kTile) & ~31);
   }
-#pragma unroll
-  for (int i = 0; i < 15; ++i) {
-    ga[i] = g[i].x;
-    gb[i] = g[i].y;
-  }
-  store_g<kAB, S>(dst, idx, na, ga);
-  store_g<kAB, S>(dst, idx + kTile, nb2, gb);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dst[phiu_index<S>(idx, a)] = cur[a].x;
-    dst[phiu_index<S>(idx + kTile, a)] = cur[a].y;
-  }
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    fa[i] = f[i].x;
-    fb[i] = f[i].y;
-  }
-  store_f<kAB, S>(dst, idx, na, fa);
-  store_f<kAB, S>(dst, idx + kTile, nb2, fb);
+  store_pair<P, S>(dst, geo, idx, na, nb2, g, f, cur);
 }
 
 // Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
@@ -896,6 +878,12 @@ void collide_variant(const float* src, float* dst, const float* phi, const float
     if (pattern == kAB && geo.pairs && geo.stage && err)                                    \
       k_collide2t<VAR, S, false><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,   \
                                                                prev, err, polls, nullptr);  \
+    else if (pattern == kAAEven && geo.pairs && geo.stage && err)                           \
+      k_collide2t<VAR, S, false, kAAEven><<<blocks, kBlock / 2, 0, st>>>(                   \
+          src, dst, phi, mu, geo, ph, prev, err, polls, nullptr);                           \
+    else if (pattern == kAAOdd && geo.pairs && geo.stage && err)                            \
+      k_collide2t<VAR, S, false, kAAOdd><<<blocks, kBlock / 2, 0, st>>>(                    \
+          src, dst, phi, mu, geo, ph, prev, err, polls, nullptr);                           \
     else if (pattern == kAB && geo.pairs)                                                   \
       k_collide2<VAR, S, false><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph,     \
                                                                prev, nullptr);              \
@@ -970,8 +958,16 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
       k_collide2<0, kF32, true><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, prev, parts);
   } else if ((pattern == kAAEven || pattern == kAAOdd) && geo.pairs) {
     const unsigned blocks = blocks_for(geo.n);
+    const bool staged = geo.stage && err;
 #define LBM_SUMS_AA(S)                                                                        \
-  if (pattern == kAAEven)                                                                     \
+  if (pattern == kAAEven && staged)                                                           \
+    k_collide2t<0, S, true, kAAEven><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo,    \
+                                                                    ph, prev, err, polls,      \
+                                                                    parts);                    \
+  else if (staged)                                                                            \
+    k_collide2t<0, S, true, kAAOdd><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, \
+                                                                   prev, err, polls, parts);  \
+  else if (pattern == kAAEven)                                                                \
     k_collide2<0, S, true, kAAEven><<<blocks, kBlock / 2, 0, st>>>(src, dst, phi, mu, geo, ph, \
                                                                    prev, parts);              \
   else                                                                                        \

@@ -79,7 +79,7 @@ def test_pairs_only_where_they_apply(L):
     w = _workload("walls", seed=23)
     with L.Solver(w, pattern=L.LBM_PATTERN_AA) as s:
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS) == 1
-        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_STENCIL_STAGE) == 0  # two-array only
+        assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_STENCIL_STAGE) == 1  # FP32 default
         with pytest.raises(L.LbmError):
             L.lbm_set_tuning(s.ctx, L.LBM_TUNE_CELL_PAIRS, 2)
 
@@ -145,18 +145,26 @@ def test_in_place_pattern_pairs(L, storage, case):
     st = L.STORAGES[storage]
     with L.Solver(w, storage=st, pattern=L.LBM_PATTERN_AA) as a, \
             L.Solver(w, storage=st, pattern=L.LBM_PATTERN_AA) as b, \
+            L.Solver(w, storage=st, pattern=L.LBM_PATTERN_AA) as d, \
             L.Solver(w, storage=st) as c:
         assert L.lbm_get_tuning(a.ctx, L.LBM_TUNE_CELL_PAIRS) == 1
+        L.lbm_set_tuning(a.ctx, L.LBM_TUNE_STENCIL_STAGE, 0)
+        L.lbm_set_tuning(d.ctx, L.LBM_TUNE_STENCIL_STAGE, 1)  # staged stencils, in place
+        assert L.lbm_get_tuning(d.ctx, L.LBM_TUNE_STENCIL_STAGE) == 1
         L.lbm_set_tuning(b.ctx, L.LBM_TUNE_CELL_PAIRS, 0)
         L.lbm_set_tuning(b.ctx, L.LBM_TUNE_GRAPHS, 0)
         for n in (1, 2, 3, 4):
-            for s in (a, b, c):
+            for s in (a, b, c, d):
                 s.step(n)
             _same(a, b)
             _same(a, c)
+            _same(a, d)
         ra = L.lbm_step_reduce(a.ctx, 3)
         rb = L.lbm_step_reduce(b.ctx, 3)
         rc = L.lbm_step_reduce(c.ctx, 3)
-        assert ra[0] == rb[0] == rc[0]
-        assert np.array_equal(ra[1], rb[1]) and np.array_equal(ra[1], rc[1])
+        rd = L.lbm_step_reduce(d.ctx, 3)
+        assert ra[0] == rb[0] == rc[0] == rd[0]
+        for r in (rb, rc, rd):
+            assert np.array_equal(ra[1], r[1])
         _same(a, c)
+        _same(a, d)
