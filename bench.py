@@ -81,14 +81,14 @@ FUSED_BYTES_PER_CELL_16 = 2 * (22 * 2 + 12) + 8
 # (8,388,608 cells), scaled by cells to the benchmark: the traffic of these kernels grows
 # in proportion to the cells.
 NCU_TRAFFIC = {
-    # 955.0 MB read + 793.2 MB written (stencil rows staged in shared memory)
-    "k_collide2t": {"bytes_per_cell": 208.41, "kernel_sha": "40d8d69168256c13"},
-    # 536.9 MB + 433.2 MB
-    "k_collide2_fp16": {"bytes_per_cell": 115.65, "kernel_sha": "40d8d69168256c13"},
-    # 856.9 MB + 794.3 MB with segments of 64 planes and no L2 prefetch (the traffic of
+    # 954.6 MB read + 793.1 MB written (stencil rows staged in shared memory)
+    "k_collide2t": {"bytes_per_cell": 208.34, "kernel_sha": "c36dbcc20c3c658c"},
+    # 536.9 MB + 432.8 MB
+    "k_collide2_fp16": {"bytes_per_cell": 115.60, "kernel_sha": "c36dbcc20c3c658c"},
+    # 856.5 MB + 799.6 MB with segments of 64 planes and no L2 prefetch (the traffic of
     # the single pass depends on both: 266.3 B per cell with 18 planes and 2 planes of
     # prefetch)
-    "k_fused": {"bytes_per_cell": 196.84, "kernel_sha": "40d8d69168256c13", "segment": 64,
+    "k_fused": {"bytes_per_cell": 197.43, "kernel_sha": "c36dbcc20c3c658c", "segment": 64,
                 "prefetch": 0},
 }
 
@@ -503,27 +503,39 @@ def run_ours(args):
             if v[4] != 0 or not np.isfinite(v[:4]).all():
                 raise RuntimeError(f"e2e run diverged: sums {v[:5]}")
 
+        def run(n):
+            """Upload, n steps with their sums, read-out; the host times of each part."""
+            t0 = time.perf_counter()
+            L.lbm_init_phi(ctx, phi_host)
+            t1 = time.perf_counter()
+            for k in range(n):
+                slot = k & 1
+                if k >= 2:
+                    check_sums(slot)
+                L.lbm_step_reduce_async(ctx, 1, sums_dev[slot].data_ptr())  # step + its sums
+                with torch.cuda.stream(stream):
+                    sums_host[slot].copy_(sums_dev[slot], non_blocking=True)
+                    arrived[slot].record(stream)
+            for k in range(max(0, n - 2), n):
+                check_sums(k & 1)
+            t2 = time.perf_counter()
+            out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P,
+                                    out=outs)
+            t3 = time.perf_counter()
+            assert np.isfinite(out["phi"]).all()
+            return t3 - t0, (t1 - t0, t2 - t1, t3 - t2)
+
+        run(4)  # untimed: the library's device staging buffers come from the allocator's cache
         barrier()
-        t0 = time.perf_counter()
-        L.lbm_init_phi(ctx, phi_host)
-        for k in range(nsteps):
-            slot = k & 1
-            if k >= 2:
-                check_sums(slot)
-            L.lbm_step_reduce_async(ctx, 1, sums_dev[slot].data_ptr())  # step + its sums
-            with torch.cuda.stream(stream):
-                sums_host[slot].copy_(sums_dev[slot], non_blocking=True)
-                arrived[slot].record(stream)
-        for k in range(max(0, nsteps - 2), nsteps):
-            check_sums(k & 1)
-        out = L.lbm_read_fields(ctx, L.LBM_FIELD_PHI | L.LBM_FIELD_U | L.LBM_FIELD_P, out=outs)
+        t_e2e, parts = run(nsteps)
         barrier()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
-        assert np.isfinite(out["phi"]).all()
+        t_e2e = max_over_ranks(t_e2e)
         return {"value": round(aggregate_mlups(cells, nsteps, world, t_e2e), 3), "unit": UNIT,
                 "h2d_bytes_per_step": round(8 * cells / nsteps),
                 "d2h_bytes_per_step": round(5 * 8 + 5 * 8 * cells / nsteps),
-                "steps": nsteps, "seconds": round(t_e2e, 4)}
+                "steps": nsteps, "seconds": round(t_e2e, 4),
+                "upload_ms": round(1e3 * parts[0], 2), "steps_ms": round(1e3 * parts[1], 2),
+                "readout_ms": round(1e3 * parts[2], 2)}
 
     e2e = None
     e2e_sustained = None
