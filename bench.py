@@ -555,6 +555,7 @@ def run_ours(args):
         runs = [("fp16", "ab", "fp16"), ("bf16", "ab", "bf16")]
         if args.pattern == "ab":
             runs.append(("aa", "aa", "fp32"))  # in place: half the state memory
+            runs.append(("aa_fp16", "aa", "fp16"))  # in place with 16-bit populations
             runs.append(("single_pass", "ab", "fp32"))  # one kernel per step (LBM_TUNE_FUSED)
         for name, pattern, storage in runs:
             wide_v = storage == "fp32"
@@ -598,8 +599,8 @@ def run_ours(args):
                 entry["segment_planes"] = L.lbm_get_tuning(vs.ctx, L.LBM_TUNE_FUSED_SEGMENT)
                 pattern_variants[name] = entry
             elif pattern == "aa":
-                for key, pat in (("context_gb", pattern), ("context_gb_ab", "ab")):
-                    grid_p, params_p = L.params_from_workload(w, pat, storage)
+                for key, pat, sto in (("context_gb", pattern, storage), ("context_gb_ab", "ab", "fp32")):
+                    grid_p, params_p = L.params_from_workload(w, pat, sto)
                     entry[key] = round(L.lbm_memory_bytes(grid_p, params_p) / 1e9, 2)
                 pattern_variants[name] = entry
             else:
