@@ -207,6 +207,17 @@ lbm_status lbm_reduce_async(lbm_ctx* ctx, double* out_dev);
 lbm_status lbm_read_state(lbm_ctx* ctx, float* f, float* g, float* phiu_prev,
                           long long* step);
 
+/* The same state at `count` listed cells only: cells[k] is the linear index
+ * x + nx (y + ny z) of a cell (host array, caller-owned, each in [0, nx ny nz), else
+ * LBM_EINVAL and nothing is read); f (7 count), g (15 count) and phiu_prev (3 count)
+ * receive the values lbm_read_state gives for those cells, planar by population
+ * (f[i count + k] is f_i of cells[k]).  Any output may be NULL; count may be 0.  For
+ * probes and for checks on grids whose whole state would not fit in host memory.
+ * Uses a device buffer of 108 bytes per listed cell for the call's duration
+ * (LBM_ENOMEM if the allocator refuses it).  Synchronises the stream. */
+lbm_status lbm_read_state_at(lbm_ctx* ctx, const long long* cells, long long count, float* f,
+                             float* g, float* phiu_prev, long long* step);
+
 /* Replace the state (same layout as lbm_read_state).  When phiu_prev is NULL or step
  * is 0, the next step takes d_t(phi u) = 0, as after lbm_init_phi.  Resuming from a
  * state read by lbm_read_state reproduces the original run bit for bit.  Synchronises

@@ -294,7 +294,7 @@ size_t step_parts_bytes(long long n) {
 // storage on grids the single-pass step takes).
 bool wants_phi_alt(const lbm_grid& g, const lbm_params& p) {
   return p.storage != LBM_STORAGE_FP32 && p.pattern == LBM_PATTERN_AB && g.nx % lbm::kTile == 0 &&
-         g.ny % 8 == 0 &&
+         g.ny % 8 == 0 && g.ny / 8 <= 65535 && g.nz <= 65535 &&
          static_cast<long long>(g.ny) * (g.nx / lbm::kTile) * lbm::tile_bytes<lbm::kF32>() <
              (1LL << 31);
 }
@@ -796,6 +796,46 @@ lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long
   }
   if (phiu_prev && !c->have_prev) std::memset(phiu_prev, 0, 3 * n * sizeof(float));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (step) *step = c->step;
+  return LBM_OK;
+}
+
+lbm_status lbm_read_state_at(lbm_ctx* c, const long long* cells, long long count, float* f,
+                             float* g, float* phiu_prev, long long* step) {
+  if (!c) return LBM_EINVAL;
+  if (const lbm_status rs = check_ready(c); rs != LBM_OK) return rs;
+  if (count < 0) return fail(c, LBM_EINVAL, "count must be >= 0");
+  if (count > 0 && !cells) return fail(c, LBM_EINVAL, "cells must not be NULL");
+  for (long long k = 0; k < count; ++k)
+    if (cells[k] < 0 || cells[k] >= c->geo.n)
+      return fail(c, LBM_EINVAL, "cell index " + std::to_string(cells[k]) + " outside the grid");
+  if (count > 0 && (f || g || (phiu_prev && c->have_prev))) {
+    const size_t idx_bytes = static_cast<size_t>(count) * sizeof(long long);
+    const size_t out_floats = static_cast<size_t>(count) * lbm::kTileSlots;
+    char* buf = static_cast<char*>(dev_alloc(c, idx_bytes + out_floats * sizeof(float)));
+    if (!buf) return fail(c, LBM_ENOMEM, "device allocation failed (cell gather)");
+    long long* d_cells = reinterpret_cast<long long*>(buf);
+    float* d_out = reinterpret_cast<float*>(buf + idx_bytes);
+    const size_t cnt = static_cast<size_t>(count);
+    cudaError_t e = cudaMemcpyAsync(d_cells, cells, idx_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = lbm::launch_gather_at(cur_state(c), c->phi, d_cells, count, d_out, c->geo,
+                                read_pattern(c), c->stream);
+    if (e == cudaSuccess && f)
+      e = cudaMemcpyAsync(f, d_out, 7 * cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && g)
+      e = cudaMemcpyAsync(g, d_out + 7 * cnt, 15 * cnt * sizeof(float), cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess && phiu_prev && c->have_prev)
+      e = cudaMemcpyAsync(phiu_prev, d_out + lbm::kSlotPhiu * cnt, 3 * cnt * sizeof(float),
+                          cudaMemcpyDeviceToHost, c->stream);
+    const cudaError_t es = cudaStreamSynchronize(c->stream);
+    dev_free(c, buf);
+    if (e != cudaSuccess) return fail_cuda(c, "lbm_read_state_at", e);
+    if (es != cudaSuccess) return fail_cuda(c, "lbm_read_state_at", es);
+  }
+  if (phiu_prev && !c->have_prev && count > 0)
+    std::memset(phiu_prev, 0, 3 * static_cast<size_t>(count) * sizeof(float));
   if (step) *step = c->step;
   return LBM_OK;
 }

@@ -299,8 +299,11 @@ cudaError_t launch_fused_s(const float* src, float* dst, const float* phi_in, fl
 
 }  // namespace
 
+// Whole blocks in x and y, and a grid whose y and z extents (ny / 8 and the segments,
+// at least one plane each) stay within 65535.
 bool fused_shape_ok(const Geometry& geo) {
-  return geo.row_tiles > 0 && geo.nx % kFX == 0 && geo.ny % kFY == 0;
+  return geo.row_tiles > 0 && geo.nx % kFX == 0 && geo.ny % kFY == 0 && geo.ny / kFY <= 65535 &&
+         geo.nz <= 65535;
 }
 
 int fused_default_segment(const Geometry& geo, int sms) {

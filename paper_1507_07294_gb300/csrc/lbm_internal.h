@@ -51,6 +51,11 @@ cudaError_t launch_init(float* state, const float* phi, const float* mu, const f
                         float tf, cudaStream_t st);
 cudaError_t launch_gather(const float* src, const float* phi_ref, float* dense, const Geometry& geo,
                           int pattern, int slot, cudaStream_t st);
+// All slots of `count` listed cells into out[slot * count + k] (cells checked by the
+// caller to lie in [0, geo.n)).
+cudaError_t launch_gather_at(const float* src, const float* phi_ref, const long long* cells,
+                             long long count, float* out, const Geometry& geo, int pattern,
+                             cudaStream_t st);
 cudaError_t launch_scatter(float* state, const float* dense, const Geometry& geo, int pattern,
                            int slot, cudaStream_t st);
 cudaError_t launch_convert(const double* in, float* out, int n, cudaStream_t st);

@@ -159,12 +159,24 @@ __global__ void __launch_bounds__(kBlock) k_phi_rows(const float* __restrict__ s
 }
 
 // ------------------------------------------------------------------- k_mu ---------
+// The chemical-potential launches are one-dimensional over the kTX x kTY x kTZ bricks,
+// x fastest, then y, then z (the order of a three-dimensional grid), so that neither ny
+// nor nz is bounded by the 65535 limit of a grid's y and z extents.
+__device__ __forceinline__ void brick_of(int b, int nbx, int nby, int& bx, int& by, int& bz) {
+  const int r = b / nbx;
+  bx = b - r * nbx;
+  bz = r / nby;
+  by = r - bz * nby;
+}
+
 template <bool D3Q7>
 __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
                                                  float* __restrict__ mu, Geometry geo,
                                                  Physics ph) {
   __shared__ float tile[kHZ][kHY][kHX];
-  mu_brick<D3Q7>(phi, mu, geo, ph, blockIdx.x, blockIdx.y, blockIdx.z, tile);
+  int bx, by, bz;
+  brick_of(blockIdx.x, (geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY, bx, by, bz);
+  mu_brick<D3Q7>(phi, mu, geo, ph, bx, by, bz, tile);
 }
 
 // ------------------------------------------------------------- k_mu_tma ---------
@@ -212,7 +224,9 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
   __shared__ alignas(8) unsigned long long bar_storage;
   const unsigned bar = smem_addr(&bar_storage);
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
+  int bx, by, bz;
+  brick_of(blockIdx.x, geo.nx / kTX, geo.ny / kTY, bx, by, bz);
+  const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -617,15 +631,13 @@ __global__ void __launch_bounds__(kBlock) k_init(float* state, const float* __re
 }
 
 // -------------------------------------------------- state gather / scatter --------
-// Slot `slot` of the current pre-collision state to dense[idx]: populations through
-// the pattern's addressing, phi u (slots 22..24) from the own tile.
+// Slot `slot` of cell idx of the current pre-collision state: populations through the
+// pattern's addressing, phi u (slots 22..24) from the own tile; with 16-bit storage the
+// reference phi added back to slot 0.
 template <int P, int S>
-__global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ src,
-                                                   const float* __restrict__ phi_ref,
-                                                   float* __restrict__ dense, Geometry geo,
-                                                   int slot) {
-  const int idx = blockIdx.x * kBlock + threadIdx.x;
-  if (idx >= geo.n) return;
+__device__ __forceinline__ float state_value(const float* __restrict__ src,
+                                             const float* __restrict__ phi_ref,
+                                             const Geometry& geo, int idx, int slot) {
   int x, y, z;
   cell_coords(geo, idx, x, y, z);
   const Nbr nb = make_nbr(geo, x, y, z);
@@ -647,7 +659,36 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ src
       v = src[phiu_index<S>(idx, slot - kSlotPhiu)];
   }
   if (S != kF32 && slot == 0) v += phi_ref[idx];
-  dense[idx] = v;
+  return v;
+}
+
+// Slot `slot` of every cell to dense[idx].
+template <int P, int S>
+__global__ void __launch_bounds__(kBlock) k_gather(const float* __restrict__ src,
+                                                   const float* __restrict__ phi_ref,
+                                                   float* __restrict__ dense, Geometry geo,
+                                                   int slot) {
+  const int idx = blockIdx.x * kBlock + threadIdx.x;
+  if (idx >= geo.n) return;
+  dense[idx] = state_value<P, S>(src, phi_ref, geo, idx, slot);
+}
+
+// All kTileSlots slots of `count` listed cells (indices checked against geo.n by the
+// caller): out[q * count + k] = slot q of cell cells[k].
+template <int P, int S>
+__global__ void __launch_bounds__(kBlock) k_gather_at(const float* __restrict__ src,
+                                                      const float* __restrict__ phi_ref,
+                                                      const long long* __restrict__ cells,
+                                                      long long count, float* __restrict__ out,
+                                                      Geometry geo) {
+  const long long items = count * kTileSlots;
+  const long long stride = static_cast<long long>(gridDim.x) * kBlock;
+  for (long long i = static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x; i < items;
+       i += stride) {
+    const int q = static_cast<int>(i / count);
+    const long long k = i - q * count;
+    out[i] = state_value<P, S>(src, phi_ref, geo, static_cast<int>(cells[k]), q);
+  }
 }
 
 // dense[idx] = pre-collision value of slot `slot` of cell idx, placed where a step of
@@ -783,7 +824,9 @@ __global__ void __launch_bounds__(kBlock) k_reduce_chunks(const double* __restri
   }
 }
 
-inline unsigned blocks_for(int n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
+// Blocks of kBlock threads covering n cells; 64-bit so that n + kBlock - 1 cannot wrap
+// for n up to 2^31 - 1.
+inline unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
 // Host-side dispatch of a kernel template over the pattern (FP32 storage) or the
 // 16-bit storage types (pattern AB only).
@@ -846,7 +889,8 @@ long long mu_tma_default_polls() { return kMbarSpins; }
 cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
                           const Geometry& geo, const Physics& ph, int* err, long long polls,
                           cudaStream_t st) {
-  const dim3 grid(geo.nx / kTX, geo.ny / kTY, (geo.nz + kTZ - 1) / kTZ);
+  const unsigned grid = static_cast<unsigned>(static_cast<long long>(geo.nx / kTX) * (geo.ny / kTY) *
+                                              ((geo.nz + kTZ - 1) / kTZ));
   if (ph.d3q7_stencil)
     k_mu_tma<true><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err, polls);
   else
@@ -860,7 +904,8 @@ bool mu_tma_shape_ok(const Geometry& geo) {
 
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st) {
-  const dim3 grid((geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY, (geo.nz + kTZ - 1) / kTZ);
+  const unsigned grid = static_cast<unsigned>(static_cast<long long>((geo.nx + kTX - 1) / kTX) *
+                                              ((geo.ny + kTY - 1) / kTY) * ((geo.nz + kTZ - 1) / kTZ));
   if (ph.d3q7_stencil)
     k_mu<true><<<grid, dim3(kTX, kTY), 0, st>>>(phi, mu, geo, ph);
   else
@@ -1025,6 +1070,24 @@ cudaError_t launch_init(float* state, const float* phi, const float* mu, const f
 cudaError_t launch_gather(const float* src, const float* phi_ref, float* dense, const Geometry& geo,
                           int pattern, int slot, cudaStream_t st) {
   LBM_DISPATCH(geo, pattern, k_gather, src, phi_ref, dense, geo, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_at(const float* src, const float* phi_ref, const long long* cells,
+                             long long count, float* out, const Geometry& geo, int pattern,
+                             cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const long long items = count * kTileSlots;
+  const long long need = (items + kBlock - 1) / kBlock;
+  do {
+    const unsigned blocks_ = static_cast<unsigned>(need < 4096 ? need : 4096);
+    if (geo.storage == kF16)
+      LBM_DISPATCH_P(pattern, k_gather_at, kF16, src, phi_ref, cells, count, out, geo)
+    else if (geo.storage == kBF16)
+      LBM_DISPATCH_P(pattern, k_gather_at, kBF16, src, phi_ref, cells, count, out, geo)
+    else
+      LBM_DISPATCH_P(pattern, k_gather_at, kF32, src, phi_ref, cells, count, out, geo)
+  } while (0);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,8 @@ _SIGNATURES = {
     "lbm_read_fields": (c_int, [c_void_p, c_uint, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_reduce": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lbm_read_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_longlong)]),
+    "lbm_read_state_at": (c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p, c_void_p,
+                                  POINTER(c_longlong)]),
     "lbm_write_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_longlong]),
     "lbm_get_step": (c_int, [c_void_p, POINTER(c_longlong)]),
     "lbm_set_velocity": (c_int, [c_void_p, c_int, c_double, c_double]),
@@ -324,6 +326,26 @@ def lbm_read_state(ctx: Context):
     return f, g, phiu, step.value
 
 
+def lbm_read_state_at(ctx: Context, cells):
+    """The state of lbm_read_state at listed cells only: cells is a sequence of linear
+    indices x + nx (y + ny z) or of (z, y, x) triples.  Returns (f[7, k], g[15, k],
+    phiu_prev[3, k], step), float32."""
+    lib = load_library()
+    c = np.asarray(cells, dtype=np.int64)
+    if c.ndim == 2:
+        nz, ny, nx = ctx.shape
+        c = (c[:, 0] * ny + c[:, 1]) * nx + c[:, 2]
+    c = np.ascontiguousarray(c.reshape(-1), dtype=np.int64)
+    k = c.size
+    f = np.empty((7, k), np.float32)
+    g = np.empty((15, k), np.float32)
+    phiu = np.empty((3, k), np.float32)
+    step = c_longlong()
+    _check(lib, lib.lbm_read_state_at(ctx.handle, _ptr(c), k, _ptr(f), _ptr(g), _ptr(phiu),
+                                      ctypes.byref(step)), ctx.handle)
+    return f, g, phiu, step.value
+
+
 def lbm_write_state(ctx: Context, f, g, phiu_prev=None, step: int = 0) -> None:
     lib = load_library()
     f = np.ascontiguousarray(f, dtype=np.float32)
@@ -509,6 +531,9 @@ class Solver:
 
     def state(self):
         return lbm_read_state(self.ctx)
+
+    def state_at(self, cells):
+        return lbm_read_state_at(self.ctx, cells)
 
     def set_state(self, f, g, phiu_prev=None, step=0):
         lbm_write_state(self.ctx, f, g, phiu_prev, step)

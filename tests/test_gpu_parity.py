@@ -457,3 +457,44 @@ def test_row_addressing_applicability(L):
         assert L.lbm_get_tuning(s.ctx, L.LBM_TUNE_ROWS) == 1
         with pytest.raises(L.LbmError):
             L.lbm_set_tuning(s.ctx, L.LBM_TUNE_ROWS, 2)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+@pytest.mark.parametrize("walls", [True, False])
+def test_state_at_listed_cells_matches_the_full_read(L, storage, pattern, walls):
+    """lbm_read_state_at returns, at listed cells (repeats, corners, wall planes, both
+    index forms), exactly what lbm_read_state returns there: before the first step
+    (phi u all zero), after an odd and after an even number of steps, for either
+    pattern and every storage type; cells outside the grid are refused."""
+    from dataclasses import replace
+    w = I.perturbed(replace(I.droplet(n=10, R=3.5, nx=64, ny=10, nz=9), walls_z=walls),
+                    seed=4, u_amp=0.01, p_amp=1e-3)
+    rng = np.random.default_rng(5)
+    n = w.cells
+    lin = np.concatenate([rng.integers(0, n, 300), [0, n - 1, n - 1, 63, 64, n - 64],
+                          rng.integers(0, n, 5)]).astype(np.int64)
+    zyx = np.array(sample_cells(w.shape, 40, seed=6))
+    with L.Solver(w, storage=storage, pattern=pattern) as s:
+        for steps in (0, 3, 2):
+            s.step(steps)
+            f, g, phiu, t = s.state()
+            for cells in (lin, zyx):
+                fa, ga, pa, ta = s.state_at(cells)
+                if cells.ndim == 2:
+                    z, y, x = cells.T
+                else:
+                    z, r = np.divmod(cells, w.nx * w.ny)
+                    y, x = np.divmod(r, w.nx)
+                assert ta == t
+                assert np.array_equal(fa, f[:, z, y, x])
+                assert np.array_equal(ga, g[:, z, y, x])
+                assert np.array_equal(pa, phiu[:, z, y, x])
+            if steps == 0:
+                assert not phiu.any()
+        fa, ga, pa, _ = s.state_at(np.zeros(0, np.int64))
+        assert fa.shape == (7, 0) and ga.shape == (15, 0) and pa.shape == (3, 0)
+        for bad in ([n], [-1], [0, n + 5]):
+            with pytest.raises(L.LbmError) as e:
+                s.state_at(np.array(bad, np.int64))
+            assert e.value.status == L.LBM_EINVAL
