@@ -120,12 +120,14 @@ typedef struct {
 
 /* Create a solver for `grid` and `params`.  `alloc` may be NULL (cudaMalloc is then
  * used); `cuda_stream` is a cudaStream_t or NULL.  Fails with LBM_EINVAL when a size
- * is < 1, N >= 2^31, a rate is outside (0, 2), s_1..3 differ, A is outside (0, 1/3),
- * a density or viscosity is not positive, or the storage type or pattern is unknown.
+ * is < 1, N = nx ny nz >= 2^31 - 64, a rate is outside (0, 2), s_1..3 differ, A is
+ * outside (0, 1/3), a density or viscosity is not positive, or the storage type or
+ * pattern is unknown.
  * Device memory per cell: the cell state (22 populations + phi u of the previous
  * step: 100 bytes in FP32, 56 bytes with 16-bit populations; twice for LBM_PATTERN_AB)
  * + phi + mu + 7 staging floats + the fused-sum partials, i.e. about 237 bytes (FP32,
- * AB), 137 bytes (FP32, AA) or 149 bytes (16-bit, AB); lbm_memory_bytes gives the
+ * AB), 137 bytes (FP32, AA), 149 bytes (16-bit, AB) or 93 bytes (16-bit, AA: the
+ * largest admitted grids, 200 GB at 2^31 - 128 cells); lbm_memory_bytes gives the
  * exact figure. */
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
                       const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out);
