@@ -234,8 +234,8 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * blocks per SM, set by lbm_create.
  * LBM_TUNE_MU_TMA: 1 (default) lets the chemical-potential pass fetch its halo bricks
  * with TMA tensor copies, 0 uses plain loads; the TMA path exists when nx is a multiple
- * of 32 (and >= 40), ny a multiple of 8 (and >= 10) and nz >= 18, and lbm_get_tuning
- * reports 1 only while it is in use.  Both give identical results.
+ * of 32 (and >= 40), ny a multiple of 8 (10 to 524280) and nz is 18 to 1048560, and
+ * lbm_get_tuning reports 1 only while it is in use.  Both give identical results.
  * LBM_TUNE_GRAPHS: 1 (default) lets lbm_step replay pairs of steps as CUDA graphs
  * (coupled model, after the first step, while not profiling), 0 launches every kernel;
  * identical results.  LBM_TUNE_TMA_WAIT_POLLS: how many times a block of the TMA

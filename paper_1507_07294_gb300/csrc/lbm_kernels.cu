@@ -159,14 +159,20 @@ __global__ void __launch_bounds__(kBlock) k_phi_rows(const float* __restrict__ s
 }
 
 // ------------------------------------------------------------------- k_mu ---------
-// The chemical-potential launches are one-dimensional over the kTX x kTY x kTZ bricks,
-// x fastest, then y, then z (the order of a three-dimensional grid), so that neither ny
-// nor nz is bounded by the 65535 limit of a grid's y and z extents.
-__device__ __forceinline__ void brick_of(int b, int nbx, int nby, int& bx, int& by, int& bz) {
-  const int r = b / nbx;
-  bx = b - r * nbx;
-  bz = r / nby;
-  by = r - bz * nby;
+// k_mu covers the kTX x kTY x kTZ bricks with a three-dimensional grid, or, where there
+// are more than 65535 bricks along y or z (the limit of a grid's y and z extents), with
+// a one-dimensional grid over the bricks in the same order (x fastest, then y, then z),
+// decoded here.  (k_mu_tma takes only grids of the first kind.)
+__device__ __forceinline__ void brick_of(int nbx, int nby, int& bx, int& by, int& bz) {
+  bx = blockIdx.x;
+  by = blockIdx.y;
+  bz = blockIdx.z;
+  if (gridDim.y == 1 && gridDim.z == 1) {
+    const int b = blockIdx.x, r = b / nbx;
+    bx = b - r * nbx;
+    bz = r / nby;
+    by = r - bz * nby;
+  }
 }
 
 template <bool D3Q7>
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
                                                  Physics ph) {
   __shared__ float tile[kHZ][kHY][kHX];
   int bx, by, bz;
-  brick_of(blockIdx.x, (geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY, bx, by, bz);
+  brick_of((geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY, bx, by, bz);
   mu_brick<D3Q7>(phi, mu, geo, ph, bx, by, bz, tile);
 }
 
@@ -224,9 +230,7 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
   __shared__ alignas(8) unsigned long long bar_storage;
   const unsigned bar = smem_addr(&bar_storage);
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  int bx, by, bz;
-  brick_of(blockIdx.x, geo.nx / kTX, geo.ny / kTY, bx, by, bz);
-  const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -886,11 +890,16 @@ cudaError_t launch_phi(const float* src, const float* phi_ref, float* phi, const
 
 long long mu_tma_default_polls() { return kMbarSpins; }
 
+// Grid of the k_mu launch over nbx x nby x nbz bricks (brick_of).
+static dim3 brick_grid(int nbx, int nby, int nbz) {
+  if (nby <= 65535 && nbz <= 65535) return dim3(nbx, nby, nbz);
+  return dim3(static_cast<unsigned>(static_cast<long long>(nbx) * nby * nbz));
+}
+
 cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
                           const Geometry& geo, const Physics& ph, int* err, long long polls,
                           cudaStream_t st) {
-  const unsigned grid = static_cast<unsigned>(static_cast<long long>(geo.nx / kTX) * (geo.ny / kTY) *
-                                              ((geo.nz + kTZ - 1) / kTZ));
+  const dim3 grid(geo.nx / kTX, geo.ny / kTY, (geo.nz + kTZ - 1) / kTZ);
   if (ph.d3q7_stencil)
     k_mu_tma<true><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err, polls);
   else
@@ -898,14 +907,17 @@ cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
   return cudaGetLastError();
 }
 
+// Whole bricks in x and y, and a three-dimensional grid of them (at most 65535 bricks
+// along y and z); other grids take k_mu.
 bool mu_tma_shape_ok(const Geometry& geo) {
-  return geo.nx % kTX == 0 && geo.ny % kTY == 0;
+  return geo.nx % kTX == 0 && geo.ny % kTY == 0 && geo.ny / kTY <= 65535 &&
+         (geo.nz + kTZ - 1) / kTZ <= 65535;
 }
 
 cudaError_t launch_mu(const float* phi, float* mu, const Geometry& geo, const Physics& ph,
                       cudaStream_t st) {
-  const unsigned grid = static_cast<unsigned>(static_cast<long long>((geo.nx + kTX - 1) / kTX) *
-                                              ((geo.ny + kTY - 1) / kTY) * ((geo.nz + kTZ - 1) / kTZ));
+  const dim3 grid = brick_grid((geo.nx + kTX - 1) / kTX, (geo.ny + kTY - 1) / kTY,
+                               (geo.nz + kTZ - 1) / kTZ);
   if (ph.d3q7_stencil)
     k_mu<true><<<grid, dim3(kTX, kTY), 0, st>>>(phi, mu, geo, ph);
   else
