@@ -231,7 +231,10 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
  * LBM_TUNE_PREFETCH_COLLIDE / LBM_TUNE_PREFETCH_PHI: how many thread blocks ahead the
  * fused stream-collide kernel / the order-parameter kernel prefetch cell data into L2
  * (0 disables).  Default: one wave, the number of SMs times the kernel's resident
- * blocks per SM, set by lbm_create.
+ * blocks per SM, set by lbm_create.  LBM_TUNE_PREFETCH_COLLIDE_SUMS: the same distance
+ * for the stream-collide kernel of the last step of lbm_step_reduce and
+ * lbm_step_reduce_async, which also sums the state it writes and has its own best
+ * distance (default: that of LBM_TUNE_PREFETCH_COLLIDE at creation).
  * LBM_TUNE_MU_TMA: 1 (default) lets the chemical-potential pass fetch its halo bricks
  * with TMA tensor copies, 0 uses plain loads; the TMA path exists when nx is a multiple
  * of 32 (and >= 40), ny a multiple of 8 (10 to 524280) and nz is 18 to 1048560, and
@@ -288,6 +291,7 @@ lbm_status lbm_write_state(lbm_ctx* ctx, const float* f, const float* g,
 #define LBM_TUNE_FUSED_PREFETCH 8
 #define LBM_TUNE_CELL_PAIRS 9
 #define LBM_TUNE_STENCIL_STAGE 10
+#define LBM_TUNE_PREFETCH_COLLIDE_SUMS 11
 lbm_status lbm_set_tuning(lbm_ctx* ctx, int param, int value);
 lbm_status lbm_get_tuning(const lbm_ctx* ctx, int param, int* value);
 

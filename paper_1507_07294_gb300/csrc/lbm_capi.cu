@@ -53,6 +53,7 @@ struct lbm_ctx {
   int row_tiles = 0;         // Geometry::row_tiles when LBM_TUNE_ROWS is on
   int pairs = 0;             // Geometry::pairs when LBM_TUNE_CELL_PAIRS is on
   int stage_rows = 0;        // Geometry::stage when LBM_TUNE_STENCIL_STAGE is on
+  int prefetch_sums = 0;     // Geometry::prefetch_collide of the steps that sum their result
 
   // single-pass step (lbm_fused.cu): enabled, planes per segment (0: by grid size), L2
   // prefetch distance in planes
@@ -431,8 +432,10 @@ lbm_status step_once(lbm_ctx* c, double* sums_out) {
          }));
   const bool prev = c->have_prev;
   if (c->vel_kind == LBM_VELOCITY_NONE) {
+    lbm::Geometry gs = c->geo;  // the summing kernel has its own best prefetch distance
+    gs.prefetch_collide = c->prefetch_sums;
     LBM_CK(c, timed(c, 2, [&] {
-             return sums_out ? lbm::launch_collide_sums(src, dst, c->phi, c->mu, c->geo, c->ph,
+             return sums_out ? lbm::launch_collide_sums(src, dst, c->phi, c->mu, gs, c->ph,
                                                          pat, prev, c->step_parts, c->partial,
                                                          sums_out, c->stream, error_word(c),
                                                          c->tma_polls < 0
@@ -566,6 +569,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
       c->geo.prefetch_collide =
           sms * lbm::resident_blocks_per_sm(c->geo.pairs ? 3 : 0, c->geo.storage);
+      c->prefetch_sums = c->geo.prefetch_collide;
       c->geo.prefetch_phi =
           sms * lbm::resident_blocks_per_sm(1, c->geo.storage, c->geo.row_tiles > 0);
     }
@@ -898,6 +902,7 @@ lbm_status lbm_set_tuning(lbm_ctx* c, int param, int value) {
   switch (param) {
     case LBM_TUNE_PREFETCH_COLLIDE: c->geo.prefetch_collide = value; break;
     case LBM_TUNE_PREFETCH_PHI: c->geo.prefetch_phi = value; break;
+    case LBM_TUNE_PREFETCH_COLLIDE_SUMS: c->prefetch_sums = value; break;
     case LBM_TUNE_MU_TMA:
       if (value > 1) return fail(c, LBM_EINVAL, "LBM_TUNE_MU_TMA takes 0 or 1");
       c->use_phi_map = value == 1;
@@ -943,6 +948,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, int param, int* value) {
   switch (param) {
     case LBM_TUNE_PREFETCH_COLLIDE: *value = c->geo.prefetch_collide; return LBM_OK;
     case LBM_TUNE_PREFETCH_PHI: *value = c->geo.prefetch_phi; return LBM_OK;
+    case LBM_TUNE_PREFETCH_COLLIDE_SUMS: *value = c->prefetch_sums; return LBM_OK;
     case LBM_TUNE_MU_TMA: *value = (c->have_phi_map && c->use_phi_map) ? 1 : 0; return LBM_OK;
     case LBM_TUNE_GRAPHS: *value = c->use_graphs ? 1 : 0; return LBM_OK;
     case LBM_TUNE_TMA_WAIT_POLLS:

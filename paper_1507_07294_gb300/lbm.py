@@ -39,7 +39,8 @@ VELOCITY_KINDS = {"uniform": LBM_VELOCITY_UNIFORM, "rotation": LBM_VELOCITY_ROTA
 
 (LBM_TUNE_PREFETCH_COLLIDE, LBM_TUNE_PREFETCH_PHI, LBM_TUNE_MU_TMA, LBM_TUNE_GRAPHS,
  LBM_TUNE_TMA_WAIT_POLLS, LBM_TUNE_ROWS, LBM_TUNE_FUSED, LBM_TUNE_FUSED_SEGMENT,
- LBM_TUNE_FUSED_PREFETCH, LBM_TUNE_CELL_PAIRS, LBM_TUNE_STENCIL_STAGE) = range(11)
+ LBM_TUNE_FUSED_PREFETCH, LBM_TUNE_CELL_PAIRS, LBM_TUNE_STENCIL_STAGE,
+ LBM_TUNE_PREFETCH_COLLIDE_SUMS) = range(12)
 
 KERNEL_PHI, KERNEL_MU, KERNEL_COLLIDE = 0, 1, 2
 KERNEL_NAMES = ("k_phi", "k_mu", "k_collide")

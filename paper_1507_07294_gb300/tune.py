@@ -1,10 +1,11 @@
 """Autotuning of launch parameters on a live run.
 
 The tuned parameters change only speed, never results: the L2 prefetch distances of
-the stream-collide and order-parameter kernels, and for the single-pass step its planes
-per segment and prefetch distance in planes (lbm_set_tuning).  Each candidate is
-timed with the library's CUDA-event kernel profile over a few steps of the run itself,
-so tuning advances the simulation by (number of candidates) x (warm + steps) steps.
+the stream-collide kernel (of plain steps, and of the steps that also sum their
+result), of the order-parameter kernel, and for the single-pass step its planes per
+segment and prefetch distance in planes (lbm_set_tuning).  Each candidate is timed with
+the library's CUDA-event kernel profile over a few steps of the run itself, so tuning
+advances the simulation by (number of candidates) x (warm + steps) steps.
 """
 from __future__ import annotations
 
@@ -16,28 +17,39 @@ from . import lbm as L
 DEFAULT_FRACTIONS = (0.0, 0.33, 0.5, 0.67, 0.83, 1.0, 1.17)
 
 
-def _time_kernel(ctx, kernel: int, steps: int, warm: int) -> float:
+def _time_kernel(ctx, kernel: int, steps: int, warm: int, sums: bool = False) -> float:
+    """Mean duration (ms) of `kernel` over `steps` steps after `warm` untimed ones; with
+    sums, steps that also sum their result (lbm_step_reduce, one step per call)."""
     L.lbm_step(ctx, warm)
     L.lbm_profile(ctx, True)
-    L.lbm_step(ctx, steps)
+    if sums:
+        for _ in range(steps):
+            L.lbm_step_reduce(ctx, 1, check=False)
+    else:
+        L.lbm_step(ctx, steps)
     ms, n = L.lbm_profile_read(ctx, kernel)
     L.lbm_profile(ctx, False)
     return ms / max(n, 1)
 
 
+TUNED = (("prefetch_collide", L.LBM_TUNE_PREFETCH_COLLIDE, L.KERNEL_COLLIDE, False),
+         ("prefetch_phi", L.LBM_TUNE_PREFETCH_PHI, L.KERNEL_PHI, False),
+         ("prefetch_collide_sums", L.LBM_TUNE_PREFETCH_COLLIDE_SUMS, L.KERNEL_COLLIDE, True))
+
+
 def autotune(ctx, steps: int = 8, warm: int = 2,
              fractions: Iterable[float] = DEFAULT_FRACTIONS) -> Dict[str, dict]:
-    """Pick the fastest prefetch distance for k_collide and k_phi; returns, per
-    parameter, the chosen value and the mean kernel time of every candidate (ms)."""
+    """Pick the fastest prefetch distance for k_collide (of plain steps and of summing
+    steps) and k_phi; returns, per parameter, the chosen value and the mean kernel time
+    of every candidate (ms)."""
     out = {}
-    for name, param, kernel in (("prefetch_collide", L.LBM_TUNE_PREFETCH_COLLIDE, L.KERNEL_COLLIDE),
-                                ("prefetch_phi", L.LBM_TUNE_PREFETCH_PHI, L.KERNEL_PHI)):
+    for name, param, kernel, sums in TUNED:
         base = L.lbm_get_tuning(ctx, param)
         cands = sorted({int(round(f * base)) for f in fractions})
         times = {}
         for v in cands:
             L.lbm_set_tuning(ctx, param, v)
-            times[v] = _time_kernel(ctx, kernel, steps, warm)
+            times[v] = _time_kernel(ctx, kernel, steps, warm, sums)
         best = min(times, key=times.get)
         L.lbm_set_tuning(ctx, param, best)
         out[name] = {"value": best, "default": base, "ms": {str(k): round(t, 5) for k, t in times.items()}}
@@ -47,7 +59,7 @@ def autotune(ctx, steps: int = 8, warm: int = 2,
 def tuning_steps(steps: int = 8, warm: int = 2, fractions: Optional[Iterable[float]] = None) -> int:
     """Number of time steps autotune() advances the run by."""
     n = len(set(fractions or DEFAULT_FRACTIONS))
-    return 2 * n * (steps + warm)
+    return len(TUNED) * n * (steps + warm)
 
 
 def autotune_fused(ctx, steps: int = 6, warm: int = 2,

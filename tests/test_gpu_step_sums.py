@@ -112,3 +112,21 @@ def test_async_matches_sync_and_nan_is_reported(L):
         s.step(1)
         _, _, st = L.lbm_step_reduce(s.ctx, 1, check=False)
     assert st == L.LBM_EUNSTABLE
+
+
+def test_sums_prefetch_distance_changes_speed_not_results(L):
+    """LBM_TUNE_PREFETCH_COLLIDE_SUMS starts at the plain steps' distance and, set to
+    another value (0: no prefetch), leaves the sums and the stored state bit for bit as
+    they were."""
+    w = _walled()
+    with L.Solver(w) as a, L.Solver(w) as b:
+        assert (L.lbm_get_tuning(a.ctx, L.LBM_TUNE_PREFETCH_COLLIDE_SUMS)
+                == L.lbm_get_tuning(a.ctx, L.LBM_TUNE_PREFETCH_COLLIDE) > 0)
+        L.lbm_set_tuning(b.ctx, L.LBM_TUNE_PREFETCH_COLLIDE_SUMS, 0)
+        assert L.lbm_get_tuning(b.ctx, L.LBM_TUNE_PREFETCH_COLLIDE_SUMS) == 0
+        for _ in range(3):
+            ma, ja = L.lbm_step_reduce(a.ctx, 2)
+            mb, jb = L.lbm_step_reduce(b.ctx, 2)
+            assert ma == mb and np.array_equal(ja, jb)
+        for x, y in zip(a.state()[:3], b.state()[:3]):
+            assert np.array_equal(x, y)
