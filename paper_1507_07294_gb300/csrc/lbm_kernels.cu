@@ -196,6 +196,59 @@ __global__ void __launch_bounds__(kTX* kTY) k_mu(const float* __restrict__ phi,
 // kMbarSpins polls) for its copy and returns, setting *err to at least 1 if the copy
 // landed in that second wait and to 2 if it did not.
 constexpr int kBX = kTX + 8;  // 4 columns either side; the stencil uses columns 3 .. 36
+constexpr int kMuThreads = kTX * kTY / 2;  // two rows of the brick per thread
+
+// mu of the brick's columns as mu_columns computes them, with each thread taking two
+// adjacent rows, i = 2 threadIdx.y + 1 and i + 1 of the halo tile, in paired FP32
+// instructions: per plane the two columns' four rows i - 1 .. i + 2 are loaded once
+// (12 shared-memory loads instead of 18), the in-plane x-pair sums h of those rows
+// serve the face sum of one column and the diagonal sum of the other, and the rest of
+// Eqs. 36 and 2 runs once for both cells.  Each lane's operations and their order are
+// those of mu_columns, so mu is bitwise the same.
+template <bool D3Q7>
+__device__ __forceinline__ void mu_columns_pair(const float (*tile)[kHY][kBX],
+                                                float* __restrict__ mu, const Geometry& geo,
+                                                const Physics& ph, int x0, int y0, int z0) {
+  typedef VOps<float2> O;
+  const int lane = threadIdx.x, i = 2 * threadIdx.y + 1, j = lane + 4;
+  const int x = x0 + lane, y = y0 + i - 1;  // the first row's cell; the second is y + 1
+  // the planes' partial sums of the two columns: centres c, face sums f, corner sums d
+  auto plane = [&](int l, float2& c, float2& f, float2& d) {
+    const float(*t)[kBX] = tile[l];
+    const float m0 = t[i - 1][j - 1], p0 = t[i - 1][j + 1], c0 = t[i - 1][j];
+    const float m1 = t[i][j - 1], p1 = t[i][j + 1], c1 = t[i][j];
+    const float m2 = t[i + 1][j - 1], p2 = t[i + 1][j + 1], c2 = t[i + 1][j];
+    const float m3 = t[i + 2][j - 1], p3 = t[i + 2][j + 1], c3 = t[i + 2][j];
+    const float2 h12 = O::add(make_float2(m1, m2), make_float2(p1, p2));
+    const float2 h03 = O::add(make_float2(m0, m3), make_float2(p0, p3));
+    c = make_float2(c1, c2);
+    f = O::add(h12, O::add(make_float2(c0, c1), make_float2(c2, c3)));
+    d = O::add(make_float2(h03.x, h12.x), make_float2(h12.y, h03.y));
+  };
+  float2 c0, f0, d0, c1, f1, d1;
+  plane(0, c0, f0, d0);
+  plane(1, c1, f1, d1);
+  const int nl = min(kTZ, geo.nz - z0);
+  float* out = mu + (static_cast<size_t>(z0) * geo.ny + y) * geo.nx + x;
+  const size_t zstride = static_cast<size_t>(geo.plane);
+  const float2 beta4 = O::k(4.0f * ph.beta), mkappa = O::k(-ph.kappa);
+  for (int l = 1; l <= nl; ++l) {
+    float2 c2, f2, d2;
+    plane(l + 1, c2, f2, d2);
+    const float2 faces = O::fma(O::k(-6.0f), c1, O::add(f1, O::add(c0, c2)));
+    const float2 lap =
+        D3Q7 ? faces
+             : O::fma(O::k(2.0f / 3.0f), faces,
+                      O::mul(O::k(1.0f / 12.0f), O::fma(O::k(-8.0f), c1, O::add(d0, d2))));
+    const float2 m = O::fma(O::mul(beta4, c1), O::fma(c1, c1, O::k(-1.0f)), O::mul(mkappa, lap));
+    float* o = out + (l - 1) * zstride;
+    o[0] = m.x;
+    o[geo.nx] = m.y;
+    c0 = c1; f0 = f1; d0 = d1;
+    c1 = c2; f1 = f2; d1 = d2;
+  }
+}
+
 constexpr unsigned kMuBoxBytes = kBX * kHY * kHZ * 4;
 constexpr long long kMbarSpins = 1 << 22;
 static_assert(kMuTmaBox[0] == kBX && kMuTmaBox[1] == kHY && kMuTmaBox[2] == kHZ,
@@ -222,7 +275,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long lo
 }
 
 template <bool D3Q7>
-__global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kMuThreads, 7) k_mu_tma(const __grid_constant__ CUtensorMap map,
                                                      const float* __restrict__ phi,
                                                      float* __restrict__ mu, Geometry geo,
                                                      Physics ph, int* err, long long polls) {
@@ -269,7 +322,7 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
       const int gz = ghost_z(geo, z0 - 1 + l);
       tile[l][i][jj] = __ldg(phi + (static_cast<size_t>(gz) * geo.ny + gy) * geo.nx + gx);
     };
-    const int nthreads = kTX * kTY;
+    const int nthreads = kMuThreads;
     // x faces: columns 3 and kTX + 4 of every row and plane
     for (int k = tid; k < 2 * kHZ * kHY; k += nthreads) {
       const int side = k / (kHZ * kHY), r = k - side * kHZ * kHY;
@@ -287,7 +340,7 @@ __global__ void __launch_bounds__(kTX* kTY, 7) k_mu_tma(const __grid_constant__ 
     }
     __syncthreads();
   }
-  mu_columns<D3Q7, kBX, 4>(tile, mu, geo, ph, x0, y0, z0);
+  mu_columns_pair<D3Q7>(tile, mu, geo, ph, x0, y0, z0);
 }
 
 // -------------------------------------------------------------- k_collide ---------
@@ -901,9 +954,9 @@ cudaError_t launch_mu_tma(const CUtensorMap& map, const float* phi, float* mu,
                           cudaStream_t st) {
   const dim3 grid(geo.nx / kTX, geo.ny / kTY, (geo.nz + kTZ - 1) / kTZ);
   if (ph.d3q7_stencil)
-    k_mu_tma<true><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err, polls);
+    k_mu_tma<true><<<grid, dim3(kTX, kTY / 2), 0, st>>>(map, phi, mu, geo, ph, err, polls);
   else
-    k_mu_tma<false><<<grid, dim3(kTX, kTY), 0, st>>>(map, phi, mu, geo, ph, err, polls);
+    k_mu_tma<false><<<grid, dim3(kTX, kTY / 2), 0, st>>>(map, phi, mu, geo, ph, err, polls);
   return cudaGetLastError();
 }
 
