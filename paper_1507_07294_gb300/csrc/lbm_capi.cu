@@ -343,10 +343,32 @@ cudaError_t timed(lbm_ctx* c, int kernel, F&& launch) {
 }
 
 // Copy N floats of a device plane to host doubles.
-// Widen an FP32 device plane to double on the device (into wide, n doubles) and copy
-// it into the caller's host buffer; asynchronous on the context's stream.
+// The device address of a caller's host buffer when it is page-locked (cudaHostAlloc,
+// cudaHostRegister, PyTorch's pinned tensors): kernels then read or store it directly
+// over the host link; nullptr for pageable memory.
+template <typename T>
+T* device_view(T* host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();  // a pointer CUDA does not know: clear the error it reported
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<T*>(a.devicePointer) : nullptr;
+}
+
+// Widen an FP32 device plane to double into the caller's host buffer, asynchronous on
+// the context's stream: straight into it when it is page-locked (the widening kernel
+// stores over the host link), else on the device into wide (n doubles) and a copy.
+// (On the GB300 host, copy-engine copies to the host after a long run of steps were
+// slow -- 12 to 45 ms for 537 MB after 1000 to 9000 steps, 2.8 ms when repeated --
+// while the kernel's own stores ran at their usual ~190 GB/s.)
 lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, double* wide) {
   const size_t n = static_cast<size_t>(c->geo.n);
+  if (double* view = device_view(host)) {
+    LBM_CK(c, lbm::launch_widen(dev, view, c->geo.n, c->stream));
+    return LBM_OK;
+  }
+  if (!wide) return fail(c, LBM_EINVAL, "read-out buffer changed from page-locked to pageable");
   LBM_CK(c, lbm::launch_widen(dev, wide, c->geo.n, c->stream));
   LBM_CK(c, cudaMemcpyAsync(host, wide, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return LBM_OK;
@@ -621,9 +643,18 @@ lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const do
   if (!phi) return fail(c, LBM_EINVAL, "phi must not be NULL");
   const size_t n = static_cast<size_t>(c->geo.n);
   const size_t s = c->geo.stride;
-  double* tmp = static_cast<double*>(dev_alloc(c, n * sizeof(double)));
-  if (!tmp) return fail(c, LBM_ENOMEM, "device allocation failed (init staging)");
+  // page-locked inputs are read by the narrowing kernel itself over the host link;
+  // pageable ones are copied to a device buffer first
+  const bool pageable = !device_view(phi) ||
+                        (u && (!device_view(u) || !device_view(u + n) || !device_view(u + 2 * n))) ||
+                        (p && !device_view(p));
+  double* tmp = nullptr;
+  if (pageable) {
+    tmp = static_cast<double*>(dev_alloc(c, n * sizeof(double)));
+    if (!tmp) return fail(c, LBM_ENOMEM, "device allocation failed (init staging)");
+  }
   auto upload = [&](const double* host, float* dst) -> cudaError_t {
+    if (const double* view = device_view(host)) return lbm::launch_convert(view, dst, c->geo.n, c->stream);
     cudaError_t e = cudaMemcpyAsync(tmp, host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
     return lbm::launch_convert(tmp, dst, c->geo.n, c->stream);
@@ -640,7 +671,7 @@ lbm_status lbm_init_phi(lbm_ctx* c, const double* phi, const double* u, const do
                          p ? c->stage + 3 * s : nullptr, c->geo, c->ph, read_pattern(c),
                          velocity_time_factor(c, 0), c->stream);
   const cudaError_t es = cudaStreamSynchronize(c->stream);
-  dev_free(c, tmp);
+  if (tmp) dev_free(c, tmp);
   if (e != cudaSuccess) return fail_cuda(c, "lbm_init_phi", e);
   if (es != cudaSuccess) return fail_cuda(c, "lbm_init_phi", es);
   c->step = 0;
@@ -729,8 +760,17 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   if (mask & (LBM_FIELD_RHO | LBM_FIELD_P | LBM_FIELD_U))
     LBM_CK(c, lbm::launch_fields(cur_state(c), phi_now, mu_now, c->stage, c->geo, c->ph,
                                  read_pattern(c), velocity_time_factor(c, c->step), c->stream));
-  double* wide = static_cast<double*>(dev_alloc(c, n * sizeof(double)));
-  if (!wide) return fail(c, LBM_ENOMEM, "device allocation failed (read-out staging)");
+  const bool pageable = ((mask & LBM_FIELD_PHI) && !device_view(phi)) ||
+                        ((mask & LBM_FIELD_MU) && !device_view(mu)) ||
+                        ((mask & LBM_FIELD_RHO) && !device_view(rho)) ||
+                        ((mask & LBM_FIELD_P) && !device_view(p)) ||
+                        ((mask & LBM_FIELD_U) &&
+                         (!device_view(u) || !device_view(u + n) || !device_view(u + 2 * n)));
+  double* wide = nullptr;
+  if (pageable) {
+    wide = static_cast<double*>(dev_alloc(c, n * sizeof(double)));
+    if (!wide) return fail(c, LBM_ENOMEM, "device allocation failed (read-out staging)");
+  }
   lbm_status st = LBM_OK;
   if (mask & LBM_FIELD_PHI) st = plane_to_host(c, phi_now, phi, wide);
   if (st == LBM_OK && (mask & LBM_FIELD_MU)) st = plane_to_host(c, mu_now, mu, wide);
@@ -742,7 +782,7 @@ lbm_status lbm_read_fields(lbm_ctx* c, unsigned mask, double* phi, double* rho, 
   if (st == LBM_OK)
     LBM_CK(c, cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   const cudaError_t es = cudaStreamSynchronize(c->stream);
-  dev_free(c, wide);
+  if (wide) dev_free(c, wide);
   if (st != LBM_OK) return st;
   if (es != cudaSuccess) return fail_cuda(c, "lbm_read_fields", es);
   return take_device_error(c, h);
