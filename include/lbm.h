@@ -103,8 +103,9 @@ typedef struct {
 
 /* Device allocator.  alloc returns device memory of at least `bytes` bytes (aligned
  * to 256 bytes) or NULL; free releases it.  Calls happen inside lbm_create,
- * lbm_init_phi and lbm_read_fields (one transient staging buffer each) and
- * lbm_destroy only. */
+ * lbm_init_phi and lbm_read_fields (one transient staging buffer each, for pageable
+ * host buffers only), lbm_read_state_at (the listed cells' buffer) and lbm_destroy
+ * only. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
@@ -136,7 +137,9 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
  * and p (N); NULL means zero.  mu follows from phi by Eq. 2 with the stencil of
  * Eq. 36; f and g are set to their equilibria f^eq (Eq. 5) and g^eq (Eq. 21).  Resets
  * the step count to 0; the first step after it takes d_t(phi u) = 0 (Eq. 34 has no
- * earlier value).  Synchronises the stream. */
+ * earlier value).  Page-locked inputs are read by the narrowing kernel directly;
+ * pageable ones are first copied through a temporary device buffer of N doubles from
+ * the context's allocator.  Synchronises the stream. */
 lbm_status lbm_init_phi(lbm_ctx* ctx, const double* phi, const double* u, const double* p);
 
 /* Prescribed velocity fields for lbm_set_velocity. */
@@ -165,10 +168,11 @@ lbm_status lbm_step(lbm_ctx* ctx, int n);
 /* Macroscopic fields at the current time, computed on the device from the current
  * populations: phi (Eq. 13), rho (Eq. 14), p (Eq. 30), u (Eq. 29, planar 3N) and mu
  * (Eq. 2).  Only the fields selected in `mask` are written; the others may be NULL.
- * Values are computed in FP32 and widened to double on the device, then copied into
- * the caller's buffers (page-locked buffers copy fastest); the widening takes n doubles
- * of temporary device memory from the context's allocator (LBM_ENOMEM if refused).
- * Synchronises the stream. */
+ * Values are computed in FP32 and widened to double on the device.  Page-locked
+ * buffers (cudaHostAlloc, cudaHostRegister) receive them straight from the widening
+ * kernel, which stores into host memory; when any selected buffer is pageable, the
+ * values go through n doubles of temporary device memory from the context's allocator
+ * (LBM_ENOMEM if refused) and a copy.  Synchronises the stream. */
 lbm_status lbm_read_fields(lbm_ctx* ctx, unsigned mask, double* phi, double* rho,
                            double* p, double* u, double* mu);
 
