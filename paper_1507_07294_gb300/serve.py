@@ -343,23 +343,19 @@ class GpuEngine:
             self.batch.step(solvers, n)
 
     def check(self, solver) -> None:
-        """Enqueues the run's FP64 sums (lbm_reduce_async) and their copy to the host."""
-        torch = self.torch
+        """Enqueues the run's FP64 sums (lbm_reduce_async), written by the reduction
+        straight into a page-locked host slot."""
         slot = self._checks.get(id(solver))
         if slot is None:
-            slot = (torch.zeros(5, dtype=torch.float64, device="cuda"),
-                    torch.zeros(5, dtype=torch.float64).pin_memory())
+            slot = self.torch.zeros(5, dtype=self.torch.float64).pin_memory()
             self._checks[id(solver)] = slot
-        st = self.stream_of(solver)
-        with torch.cuda.stream(st):
-            self.lbm.lbm_reduce_async(solver.ctx, slot[0].data_ptr())
-            slot[1].copy_(slot[0], non_blocking=True)
+        self.lbm.lbm_reduce_async(solver.ctx, slot.data_ptr())
 
     def diverged(self, solver) -> bool:
         """Whether the last check of the run (read after its fence) found a non-finite
         value."""
         slot = self._checks.get(id(solver))
-        return slot is not None and bool(slot[1][4].item() > 0)
+        return slot is not None and bool(slot[4].item() > 0)
 
     def fence(self, solvers):
         """Events marking everything launched so far on the runs' streams."""
@@ -388,7 +384,13 @@ class GpuEngine:
                 if e.status != lbm.LBM_EUNSTABLE:
                     raise
                 totals, stable = None, False
-            phi = solver.fields(lbm.LBM_FIELD_PHI)["phi"] if self.keep_phi else None
+            phi = None
+            if self.keep_phi:
+                # a page-locked buffer (from PyTorch's cache of them), which the read-out
+                # kernel fills directly
+                buf = self.torch.empty(solver.ctx.n, dtype=self.torch.float64,
+                                       pin_memory=True).numpy()
+                phi = lbm.lbm_read_fields(solver.ctx, lbm.LBM_FIELD_PHI, out={"phi": buf})["phi"]
         solver.close()
         self._checks.pop(id(solver), None)
         self._free_streams.append(self._stream_of.pop(id(solver)))
