@@ -209,7 +209,9 @@ lbm_status lbm_reduce_async(lbm_ctx* ctx, double* out_dev);
  * current time just after propagation, f (7N) and g (15N), planar by population, and
  * the phi u of the previous step (3N, planar; all zero while no step has been taken
  * since lbm_init_phi).  FP32 exactly as stored.  Any output may be NULL.  `step`
- * receives the step count.  Synchronises the stream. */
+ * receives the step count.  Page-locked outputs are written by the gathering kernel
+ * directly, pageable ones through the context's staging plane and a copy.
+ * Synchronises the stream. */
 lbm_status lbm_read_state(lbm_ctx* ctx, float* f, float* g, float* phiu_prev,
                           long long* step);
 

@@ -834,6 +834,11 @@ lbm_status lbm_read_state(lbm_ctx* c, float* f, float* g, float* phiu_prev, long
     else
       dst = (phiu_prev && c->have_prev) ? phiu_prev + (q - lbm::kSlotPhiu) * n : nullptr;
     if (!dst) continue;
+    if (float* view = device_view(dst)) {  // page-locked: the gather stores into it
+      LBM_CK(c, lbm::launch_gather(cur_state(c), c->phi, view, c->geo, read_pattern(c), q,
+                                   c->stream));
+      continue;
+    }
     LBM_CK(c, lbm::launch_gather(cur_state(c), c->phi, c->stage, c->geo, read_pattern(c), q,
                                  c->stream));
     LBM_CK(c, cudaMemcpyAsync(dst, c->stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));

@@ -355,6 +355,20 @@ def test_page_locked_host_buffers_give_the_same_values(L):
         assert np.array_equal(got[k], ref[k]), k
     for k in ("phi", "u"):
         assert np.array_equal(got2[k], ref[k]), k
+    # the state read into page-locked arrays
+    import ctypes
+    with L.Solver(w) as d:
+        d.step(3)
+        want = d.state()
+        bufs = [torch.zeros((q,) + w.shape, dtype=torch.float32, pin_memory=True).numpy()
+                for q in (7, 15, 3)]
+        step = ctypes.c_longlong()
+        lib = L.load_library()
+        assert lib.lbm_read_state(d.ctx.handle, *(b.ctypes.data_as(ctypes.c_void_p) for b in bufs),
+                                  ctypes.byref(step)) == L.LBM_OK
+    assert step.value == want[3] == 3
+    for x, y in zip(bufs, want[:3]):
+        assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("shape, walls", [((64, 16, 24), False), ((64, 16, 18), True),
