@@ -57,12 +57,8 @@ LINES = {
 def test_bench_line_at_full_size_one_step(L, line):
     cfg = LINES[line]
     storage = cfg.get("storage", "fp32")
-    if cfg.get("tracking"):
-        w = I.deformation(n=256)
-        warm = 9
-    else:
-        w = _rt256(**cfg.get("variant", {}))
-        warm = 9
+    w = I.deformation(n=256) if cfg.get("tracking") else _rt256(**cfg.get("variant", {}))
+    warm = 9
     p = O.Params.from_workload(w)
     cells = sample_cells(w.shape, 100, seed=41)
     with L.Solver(w, pattern=cfg.get("pattern", "ab"), storage=storage) as s:

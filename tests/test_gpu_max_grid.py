@@ -20,6 +20,7 @@ Skipped when the GPU has less than the context plus the 17 GB FP64 upload buffer
 or the host less than about 30 GB of memory available.
 """
 import gc
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -45,16 +46,20 @@ def _host_available_bytes() -> int:
     return 0
 
 
+@pytest.fixture(scope="module")
+def L():
+    from paper_1507_07294_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
 def _small_workload():
     w = I.droplet(n=PY, R=5.0, D=4.0, nx=PX, ny=PY, nz=PZ)
     return I.perturbed(w, seed=31, phi_amp=0.05)
 
 
-def test_largest_admitted_grid_equals_its_period():
+def test_largest_admitted_grid_equals_its_period(L):
     import torch
-    from dataclasses import replace
-    from paper_1507_07294_gb300 import lbm as L
-    L.load_library()
     n = NX * NY * NZ
     assert n == 2 ** 31 - 128
 
@@ -117,14 +122,11 @@ def test_largest_admitted_grid_equals_its_period():
 
 @pytest.mark.parametrize("shape,period", [((1100 * 1000, 1, 1), (1100, 1, 1)),
                                           ((2, 600 * 1000, 1), (2, 600, 1))])
-def test_long_thin_grids_equal_their_period(shape, period):
+def test_long_thin_grids_equal_their_period(L, shape, period):
     """Grids longer than 65535 bricks of the chemical-potential pass in z (nz > 1048560)
     or in y (ny > 524280): a column of 1.1M cells and a strip of 0.6M rows, periodic,
     with an initial condition of period 1100 (600) along their long axis, step exactly
     as the one-period grid does, bit for bit, at every cell."""
-    from dataclasses import replace
-    from paper_1507_07294_gb300 import lbm as L
-    L.load_library()
     nz, ny, nx = shape
     pz, py, px = period
     rng = np.random.default_rng(33)
