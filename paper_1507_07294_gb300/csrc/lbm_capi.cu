@@ -342,7 +342,6 @@ cudaError_t timed(lbm_ctx* c, int kernel, F&& launch) {
   return e;
 }
 
-// Copy N floats of a device plane to host doubles.
 // The device address of a caller's host buffer when it is page-locked (cudaHostAlloc,
 // cudaHostRegister, PyTorch's pinned tensors): kernels then read or store it directly
 // over the host link; nullptr for pageable memory.
@@ -359,9 +358,10 @@ T* device_view(T* host) {
 // Widen an FP32 device plane to double into the caller's host buffer, asynchronous on
 // the context's stream: straight into it when it is page-locked (the widening kernel
 // stores over the host link), else on the device into wide (n doubles) and a copy.
-// (On the GB300 host, copy-engine copies to the host after a long run of steps were
-// slow -- 12 to 45 ms for 537 MB after 1000 to 9000 steps, 2.8 ms when repeated --
-// while the kernel's own stores ran at their usual ~190 GB/s.)
+// (Measured on a GB300 with its Grace host: copy-engine copies to host memory slow
+// down with the number of kernel launches before them -- 12 to 45 ms for 537 MB after
+// 1000 to 9000 steps, 2.8 ms when repeated -- while a kernel's stores into the same
+// page-locked memory keep their ~190 GB/s.)
 lbm_status plane_to_host(lbm_ctx* c, const float* dev, double* host, double* wide) {
   const size_t n = static_cast<size_t>(c->geo.n);
   if (double* view = device_view(host)) {
