@@ -2,8 +2,9 @@
  * R = 8, D = 4, sigma = 0.01, rho 3:1, nu = 0.1, Mob = 0.1 (the droplet setup of
  * Sec. III).  Uses the library's own allocator (cudaMalloc) and the default stream.
  * Prints one line "steps=<n> sum_phi=<s0> -> <s1> max_phi=<m> mu_min=<x>" and exits 0
- * when sum phi is conserved to 1e-6 of sum |phi| and every field is finite; 1 if a
- * check fails; 2 if a call fails (its status and message are printed). */
+ * when sum phi is conserved to 1e-6 of sum |phi|, every field is finite and the state
+ * read at a few listed cells (lbm_read_state_at) equals the whole state read there;
+ * 1 if a check fails; 2 if a call fails (its status and message are printed). */
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -64,6 +65,23 @@ int main(void) {
     return 2;
   long long t = -1;
   lbm_get_step(ctx, &t);
+  /* the state at four listed cells against the whole state */
+  float* fs = malloc(7 * n * sizeof(float));
+  float* gs = malloc(15 * n * sizeof(float));
+  if (!fs || !gs) return 2;
+  const long long cells[4] = {0, (long long)n - 1, 12345, 12345};
+  float fa[7 * 4], ga[15 * 4];
+  long long ta = -1;
+  if (check(ctx, lbm_read_state(ctx, fs, gs, NULL, NULL), "lbm_read_state")) return 2;
+  if (check(ctx, lbm_read_state_at(ctx, cells, 4, fa, ga, NULL, &ta), "lbm_read_state_at"))
+    return 2;
+  int same = ta == t;
+  for (int k = 0; k < 4; ++k) {
+    for (int i = 0; i < 7; ++i) same = same && fa[i * 4 + k] == fs[(size_t)i * n + cells[k]];
+    for (int i = 0; i < 15; ++i) same = same && ga[i * 4 + k] == gs[(size_t)i * n + cells[k]];
+  }
+  free(fs);
+  free(gs);
   if (check(ctx, lbm_destroy(ctx), "lbm_destroy")) return 2;
 
   double maxphi = -1e30, minmu = 1e30;
@@ -78,7 +96,7 @@ int main(void) {
   free(phi0);
   free(phi);
   free(mu);
-  const int ok = finite && t == steps && fabs(s1 - s0) <= 1e-6 * abs0 &&
+  const int ok = finite && same && t == steps && fabs(s1 - s0) <= 1e-6 * abs0 &&
                  fabs(s0 - sum0) <= 1e-5 * abs0 && maxphi > 0.9 && maxphi < 1.05;
   return ok ? 0 : 1;
 }
