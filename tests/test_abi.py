@@ -111,3 +111,14 @@ def test_size_bound_of_the_grid():
     with pytest.raises(L.LbmError) as e:
         L.lbm_memory_bytes(L.LbmGrid(64, 31, 1082401, 0), params)  # 2^31 - 64 cells
     assert e.value.status == L.LBM_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define and status value of include/lbm.h has the same value in the
+    Python binding."""
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    consts = dict(re.findall(r"^#define (LBM_[A-Z0-9_]+)\s+([0-9]+)u?\b", text, re.M))
+    consts.update(re.findall(r"^\s*(LBM_[A-Z]+)\s*=\s*([0-9]+)", text, re.M))
+    assert len(consts) >= 35
+    wrong = {k: (v, getattr(L, k, None)) for k, v in consts.items() if getattr(L, k, None) != int(v)}
+    assert not wrong, wrong
