@@ -42,7 +42,8 @@ struct lbm_ctx {
                            // gather/scatter, initial u and p
   double* partial = nullptr;  // reduction partials
   double* red = nullptr;      // 5 reduction results; red[7] holds the device error word
-  double* step_parts = nullptr;  // per-warp partials of the fused step sums
+  float* step_parts = nullptr;   // per-warp partials of the fused step sums (FP32 sums of
+                                 // 32 cells and a count: exact in float)
 
   // TMA descriptors of phi_buf[0], phi_buf[1] for the chemical-potential pass (when the
   // grid allows it)
@@ -219,7 +220,8 @@ void release(lbm_ctx* c) {
   dev_free(c, c->red);
   dev_free(c, c->step_parts);
   c->pop[0] = c->pop[1] = c->phi = c->phi_buf[0] = c->phi_buf[1] = c->mu = c->stage = nullptr;
-  c->partial = c->red = c->step_parts = nullptr;
+  c->partial = c->red = nullptr;
+  c->step_parts = nullptr;
 }
 
 // Device error word (1: a bounded wait on a TMA copy ran out), kept in red[7].
@@ -286,9 +288,9 @@ bool encode_phi_map(lbm_ctx* c, int which) {
          CUDA_SUCCESS;
 }
 
-// Per-warp partials of the fused step sums: 5 doubles per 32 cells.
+// Per-warp partials of the fused step sums: 5 floats per 32 cells.
 size_t step_parts_bytes(long long n) {
-  return static_cast<size_t>(lbm::cell_warps(n)) * 5 * sizeof(double);
+  return static_cast<size_t>(lbm::cell_warps(n)) * 5 * sizeof(float);
 }
 
 // Whether a context of this grid and these parameters keeps a second phi array (16-bit
@@ -615,7 +617,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
   c->stage = static_cast<float*>(dev_alloc(c, plane * 7));
   c->partial = static_cast<double*>(dev_alloc(c, sizeof(double) * 5 * lbm::kReduceMaxParts));
   c->red = static_cast<double*>(dev_alloc(c, sizeof(double) * 8));
-  c->step_parts = static_cast<double*>(dev_alloc(c, step_parts_bytes(c->geo.n)));
+  c->step_parts = static_cast<float*>(dev_alloc(c, step_parts_bytes(c->geo.n)));
   if (!c->pop[0] || (params->pattern == LBM_PATTERN_AB && !c->pop[1]) || !c->phi ||
       (need_alt && !c->phi_buf[1]) || !c->mu ||
       !c->stage || !c->partial || !c->red || !c->step_parts) {

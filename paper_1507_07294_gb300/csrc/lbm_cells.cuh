@@ -573,14 +573,15 @@ __device__ __forceinline__ void collide_pair(const float* src, float* dst,
   store_pair<P, S>(dst, geo, idx, na, nb2, g, f, cur);
 }
 
-// Sums of the fused step sums over the 32 cells of a warp, stored as 5 doubles at
-// parts[5 w] (w = the warp's first cell / 32): sum phi, momentum x, y, z and the count
-// of cells with a non-finite contribution.  The four sums take 6 shuffles instead of
+// Sums of the fused step sums over the 32 cells of a warp, stored as 5 floats at
+// parts[5 w] (w = the warp's first cell / 32): sum phi, momentum x, y, z (FP32 sums)
+// and the count of cells with a non-finite contribution (exact in float); the
+// reduction over warps that follows is FP64.  The four sums take 6 shuffles instead of
 // 20: across lane bit 4 a lane keeps two values and hands its partner the other two,
 // across bit 3 one of those, so that lane l then carries value 2 (l >> 4 & 1) +
 // (l >> 3 & 1) over 4 lanes; three butterfly levels over bits 2..0 complete each sum in
 // its group of 8 lanes.  All 32 lanes must call it.
-__device__ __forceinline__ void warp_sums_store(const float s[4], bool bad, double* parts,
+__device__ __forceinline__ void warp_sums_store(const float s[4], bool bad, float* parts,
                                                 long long first_cell) {
   const unsigned nbad = __popc(__ballot_sync(0xffffffffu, bad));
   const unsigned lane = threadIdx.x & 31;
@@ -592,9 +593,9 @@ __device__ __forceinline__ void warp_sums_store(const float s[4], bool bad, doub
   float v = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
 #pragma unroll
   for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  double* out = parts + static_cast<size_t>(first_cell >> 5) * 5;
-  if ((lane & 7) == 0) out[lane >> 3] = static_cast<double>(v);
-  if (lane == 0) out[4] = static_cast<double>(nbad);
+  float* out = parts + static_cast<size_t>(first_cell >> 5) * 5;
+  if ((lane & 7) == 0) out[lane >> 3] = v;
+  if (lane == 0) out[4] = static_cast<float>(nbad);
 }
 
 }  // namespace lbm

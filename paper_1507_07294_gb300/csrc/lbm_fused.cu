@@ -118,7 +118,7 @@ constexpr int fused_min_blocks() {
 template <int S, bool SUMS>
 __global__ void __launch_bounds__(kFThreads, fused_min_blocks<S>())
     k_fused(const float* src, float* dst, const float* phi_in, float* phi_out, Geometry geo,
-            Physics ph, int have_prev, int seg, int pf, double* parts) {
+            Physics ph, int have_prev, int seg, int pf, float* parts) {
   __shared__ FusedSmem sm;
   const int tx = threadIdx.x & (kFX - 1), ty = threadIdx.x >> kTileShift;
   const int x0 = blockIdx.x * kFX, y0 = blockIdx.y * kFY;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kFThreads, fused_min_blocks<S>())
 template <int S>
 cudaError_t launch_fused_s(const float* src, float* dst, const float* phi_in, float* phi_out,
                            const Geometry& geo, const Physics& ph, bool have_prev, int seg,
-                           int pf, double* parts, cudaStream_t st) {
+                           int pf, float* parts, cudaStream_t st) {
   const dim3 grid(geo.nx / kFX, geo.ny / kFY, (geo.nz + seg - 1) / seg);
   const int prev = have_prev ? 1 : 0;
   if (parts)
@@ -320,7 +320,7 @@ int fused_default_segment(const Geometry& geo, int sms) {
 
 cudaError_t launch_fused(const float* src, float* dst, const float* phi_in, float* phi_out,
                          const Geometry& geo, const Physics& ph, bool have_prev, int seg, int pf,
-                         double* parts, double* partial, double* out, cudaStream_t st) {
+                         float* parts, double* partial, double* out, cudaStream_t st) {
   cudaError_t e;
   if (geo.storage == kF16)
     e = launch_fused_s<kF16>(src, dst, phi_in, phi_out, geo, ph, have_prev, seg, pf, parts, st);

@@ -74,16 +74,16 @@ inline size_t state_bytes(int n, int storage) {
 // Warps of a one-cell-per-thread launch over n cells (one partial each in the fused sums).
 int cell_warps(long long n);
 // Stream-collide of the default model variant that also reduces the state it writes:
-// per-warp partials into parts (5 x cell_warps(n) doubles), then the fixed-order
+// per-warp partials into parts (5 x cell_warps(n) floats), then the fixed-order
 // reduction through partial (5 x kReduceMaxParts) into out (5 doubles, as launch_reduce).
 cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
                                 const Geometry& geo, const Physics& ph, int pattern,
-                                bool have_prev, double* parts, double* partial, double* out,
+                                bool have_prev, float* parts, double* partial, double* out,
                                 cudaStream_t st, int* err = nullptr, long long polls = 0);
 
 // The fixed-order FP64 reduction of the per-warp partials of the step sums (the tail of
 // launch_collide_sums): parts -> partial -> out (5 doubles).
-cudaError_t launch_step_sums_final(const double* parts, double* partial, double* out,
+cudaError_t launch_step_sums_final(const float* parts, double* partial, double* out,
                                    const Geometry& geo, cudaStream_t st);
 
 // Single-pass step (lbm_fused.cu): pattern AB, default model variant, grids with
@@ -95,6 +95,6 @@ bool fused_shape_ok(const Geometry& geo);
 int fused_default_segment(const Geometry& geo, int sms);
 cudaError_t launch_fused(const float* src, float* dst, const float* phi_in, float* phi_out,
                          const Geometry& geo, const Physics& ph, bool have_prev, int seg, int pf,
-                         double* parts, double* partial, double* out, cudaStream_t st);
+                         float* parts, double* partial, double* out, cudaStream_t st);
 
 }  // namespace lbm

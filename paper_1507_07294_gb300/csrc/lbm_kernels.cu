@@ -372,7 +372,7 @@ template <int VAR, int S, bool SUMS, int P = kAB>
 __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
     k_collide2(const float* src, float* dst, const float* __restrict__ phi,
                const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev,
-               double* __restrict__ parts) {
+               float* __restrict__ parts) {
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
   const int idx = blockIdx.x * kBlock + (threadIdx.x >> 5) * (2 * kTile) + (threadIdx.x & 31);
   if (idx >= geo.n) return;
@@ -416,7 +416,7 @@ template <int VAR, int S, bool SUMS, int P = kAB>
 __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
     k_collide2t(const float* src, float* dst, const float* __restrict__ phi,
                 const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev, int* err,
-                long long polls, double* __restrict__ parts) {
+                long long polls, float* __restrict__ parts) {
   __shared__ alignas(128) float st[2][kStFloats];
   __shared__ alignas(8) unsigned long long bar_storage;
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kBlock / 2, collide2_min_blocks<S>())
 }
 
 // Fused stream-collide that also sums the state it writes (collide_cell with SUMS):
-// each warp leaves 5 doubles in parts[5 w ..] (w = its first cell / 32; warp_sums_store).
+// each warp leaves 5 floats in parts[5 w ..] (w = its first cell / 32; warp_sums_store).
 // The 32 cells of a warp are summed in FP32 by a fixed butterfly (FP64 throughput on
 // this GPU is a small fraction of FP32, and no block barrier holds finished warps back);
 // everything above in FP64, in a fixed order.
@@ -551,7 +551,7 @@ template <int P, int S>
 __global__ void __launch_bounds__(kBlock, collide_min_blocks<S>())
     k_collide_sums(const float* src, float* dst, const float* __restrict__ phi,
                    const float* __restrict__ mu, Geometry geo, Physics ph, int have_prev,
-                   double* __restrict__ parts) {
+                   float* __restrict__ parts) {
   prefetch_ahead<S, true>(src, phi, mu, geo, geo.prefetch_collide);
   const int idx = blockIdx.x * kBlock + threadIdx.x;
   if ((idx & ~31) >= geo.n) return;  // the whole warp lies beyond the grid
@@ -860,8 +860,8 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double* __restric
   }
 }
 
-// Block b sums parts [b chunk, (b + 1) chunk) (5 doubles each) in a fixed order.
-__global__ void __launch_bounds__(kBlock) k_reduce_chunks(const double* __restrict__ parts,
+// Block b sums parts [b chunk, (b + 1) chunk) (5 floats each) in FP64, in a fixed order.
+__global__ void __launch_bounds__(kBlock) k_reduce_chunks(const float* __restrict__ parts,
                                                           int nparts, int chunk,
                                                           double* __restrict__ out) {
   __shared__ double sh[kBlock];
@@ -1047,7 +1047,7 @@ int cell_warps(long long n) { return static_cast<int>((n + 31) / 32); }
 
 cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, const float* mu,
                                 const Geometry& geo, const Physics& ph, int pattern,
-                                bool have_prev, double* parts, double* partial, double* out,
+                                bool have_prev, float* parts, double* partial, double* out,
                                 cudaStream_t st, int* err, long long polls) {
   const int prev = have_prev ? 1 : 0;
   if (pattern == kAB && geo.pairs && geo.stage && err) {
@@ -1099,7 +1099,7 @@ cudaError_t launch_collide_sums(const float* src, float* dst, const float* phi, 
   return launch_step_sums_final(parts, partial, out, geo, st);
 }
 
-cudaError_t launch_step_sums_final(const double* parts, double* partial, double* out,
+cudaError_t launch_step_sums_final(const float* parts, double* partial, double* out,
                                    const Geometry& geo, cudaStream_t st) {
   const int nparts = cell_warps(geo.n);
   const int groups = nparts < kReduceMaxParts ? nparts : kReduceMaxParts;

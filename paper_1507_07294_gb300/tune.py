@@ -37,7 +37,7 @@ TUNED = (("prefetch_collide", L.LBM_TUNE_PREFETCH_COLLIDE, L.KERNEL_COLLIDE, Fal
          ("prefetch_collide_sums", L.LBM_TUNE_PREFETCH_COLLIDE_SUMS, L.KERNEL_COLLIDE, True))
 
 
-def autotune(ctx, steps: int = 8, warm: int = 2,
+def autotune(ctx, steps: int = 16, warm: int = 2,
              fractions: Iterable[float] = DEFAULT_FRACTIONS) -> Dict[str, dict]:
     """Pick the fastest prefetch distance for k_collide (of plain steps and of summing
     steps) and k_phi; returns, per parameter, the chosen value and the mean kernel time
@@ -56,7 +56,7 @@ def autotune(ctx, steps: int = 8, warm: int = 2,
     return out
 
 
-def tuning_steps(steps: int = 8, warm: int = 2, fractions: Optional[Iterable[float]] = None) -> int:
+def tuning_steps(steps: int = 16, warm: int = 2, fractions: Optional[Iterable[float]] = None) -> int:
     """Number of time steps autotune() advances the run by."""
     n = len(set(fractions or DEFAULT_FRACTIONS))
     return len(TUNED) * n * (steps + warm)
