@@ -198,10 +198,11 @@ class _TorchAllocator:
 class Context:
     """Handle of an lbm_ctx plus the Python objects that must outlive it."""
 
-    def __init__(self, handle: c_void_p, n: int, shape, allocator=None):
+    def __init__(self, handle: c_void_p, n: int, shape, allocator=None, stream: int = 0):
         self.handle = handle
         self.n = n
         self.shape = shape
+        self.stream = stream  # the cudaStream_t (as int) the context's work runs on
         self._allocator = allocator
 
     @property
@@ -226,7 +227,7 @@ def lbm_create(grid: LbmGrid, params: LbmParams, stream: Optional[int] = None,
                         ctypes.byref(out))
     _check(lib, st, None)
     n = grid.nx * grid.ny * grid.nz
-    return Context(out, n, (grid.nz, grid.ny, grid.nx), alloc)
+    return Context(out, n, (grid.nz, grid.ny, grid.nx), alloc, int(stream))
 
 
 def lbm_init_phi(ctx: Context, phi, u=None, p=None) -> None:

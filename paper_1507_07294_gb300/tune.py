@@ -19,14 +19,26 @@ DEFAULT_FRACTIONS = (0.0, 0.33, 0.5, 0.67, 0.83, 1.0, 1.17)
 
 def _time_kernel(ctx, kernel: int, steps: int, warm: int, sums: bool = False) -> float:
     """Mean duration (ms) of `kernel` over `steps` steps after `warm` untimed ones; with
-    sums, steps that also sum their result (lbm_step_reduce, one step per call)."""
+    sums, steps that also sum their result (lbm_step_reduce_async, one step per call,
+    back to back as a run that checks every step enqueues them)."""
     L.lbm_step(ctx, warm)
-    L.lbm_profile(ctx, True)
     if sums:
+        # the whole step, timed on the context's stream: with its sums every step
+        # launches two small reductions after the stream-collide pass, and the prefetch
+        # distance that suits the pass alone need not suit the sequence
+        import torch
+        stream = torch.cuda.ExternalStream(ctx.stream) if ctx.stream else torch.cuda.default_stream()
+        out = torch.zeros(8, dtype=torch.float64, device="cuda")
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
         for _ in range(steps):
-            L.lbm_step_reduce(ctx, 1, check=False)
-    else:
-        L.lbm_step(ctx, steps)
+            L.lbm_step_reduce_async(ctx, 1, out.data_ptr())
+        t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1) / steps
+    L.lbm_profile(ctx, True)
+    L.lbm_step(ctx, steps)
     ms, n = L.lbm_profile_read(ctx, kernel)
     L.lbm_profile(ctx, False)
     return ms / max(n, 1)
